@@ -1,0 +1,385 @@
+#!/usr/bin/env python3
+"""Benchmark of the point-cloud rasterizer (arXiv 1908.02681) on one GB300 per rank.
+
+One step = one complete frame of the hot path over the whole point cloud: atomicMin rasterization
+(Section 2.1, pass 1), the basic resolve, the high-quality splatting band accumulation (Section 2.2,
+pass 2) and the HQ resolve that also clears the framebuffer for the next frame. `value` is points per
+second through that whole frame (Gpts/s). The points are resident in HBM when the timed region starts;
+`e2e` repeats the frame through the same C ABI with the points copied from pinned host memory and both
+images copied back inside the timed region.
+
+Default workload: the 100M-point synthetic LIDAR scene (sin-sum terrain over 1 km^2 + 200 box
+buildings, 1 cm noise, height-ramp RGB, coherent scan order), 1920x1080, fov 60, near 0.1, far 3000,
+linear 40-bit depth, eps = 1 %. It stands in for the paper's scanned data sets (Table 1), which are not
+available. Inputs are 1.6 GB, larger than the 129 MB L2, so no L2 flush is needed between steps.
+
+--impl reference times the oracle (single-threaded FP64 C++) on a bounded sample of the same workload.
+Multi-GPU (torchrun): independent replicas, one full frame per rank per step (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import glob
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gpts/s atomicMin & HQ-splat, % of HBM/atomic roofline; served frames/s, p50/p99"
+BYTES_PER_POINT = 16
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _workload(name: str):
+    import scenes
+    if name == "lidar100m":
+        return dict(desc="LIDAR 100M points (1 km^2 sin-sum terrain + 200 boxes, 1 cm noise, coherent order), "
+                         "1920x1080, fov 60, near 0.1, far 3000, 40-bit linear depth, eps 1%",
+                    n=100_000_000, gen=lambda n, out: scenes.lidar(n, 2, out=out), view=scenes.lidar_1km_view())
+    if name == "lidar100m-shuffled":
+        def gen(n, out):
+            scenes.lidar(n, 2, out=out)
+            scenes.shuffle(out, 17)
+        return dict(desc="LIDAR 100M points, shuffled order, 1920x1080, 40-bit linear depth, eps 1%", n=100_000_000,
+                    gen=gen, view=scenes.lidar_1km_view())
+    if name == "cube1m":
+        return dict(desc="1M points uniform in the unit cube, 640x480, fov 60, near 0.1, far 10, 40-bit linear depth",
+                    n=1_000_000, gen=lambda n, out: scenes.cube(n, 1, out=out), view=scenes.cube_1m_view())
+    raise SystemExit(f"unknown workload {name}")
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"pcr_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _csrc_digest() -> str:
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1908_02681_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(os.path.basename(f).encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel: str, workload: str, n: int):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current kernels."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d[kernel][workload]
+        if e.get("csrc_digest") != _csrc_digest():
+            return None
+        return e["bytes_per_point"] * n
+    except Exception:
+        return None
+
+
+def cpu_oracle_frame(points, view, eps=(1, 100)):
+    """One full frame (both passes, both resolves) of the oracle; returns seconds."""
+    import oracle
+    t0 = time.perf_counter()
+    fb = oracle.render_atomicmin(points, view)
+    oracle.resolve_basic(fb)
+    acc, _ = oracle.hq_accumulate(points, view, fb, *eps)
+    oracle.resolve_hq(acc)
+    return time.perf_counter() - t0
+
+
+def run_reference(args, wl):
+    """The oracle as it stands, on host cores, on a bounded sample of the workload per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sample_n = min(wl["n"], args.reference_sample)
+    pts = np.empty((sample_n, 4), np.uint32)
+    wl["gen"](sample_n, pts)
+    for _ in range(args.warmup):
+        cpu_oracle_frame(pts, wl["view"])
+    ts = [cpu_oracle_frame(pts, wl["view"]) for _ in range(args.steps)]
+    t = sum(ts) / len(ts)
+    value = sample_n / t / 1e9
+    sample = f"first {sample_n} points of the workload (same view), full frame: both passes and resolves"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Gpts/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl["desc"], "points_per_step": sample_n},
+        "cpu_baseline": {"value": value, "unit": "Gpts/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "Gpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
+
+
+def run_ours(args, wl):
+    import torch
+    from paper_1908_02681_gb300 import build as pcr_build
+    from paper_1908_02681_gb300 import pcr
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    pcr.load()
+    n, view = wl["n"], wl["view"]
+    view.transform = {"exact": 0, "fp64": 1, "double-float": 2}[args.transform]
+    W, H = view.width, view.height
+    npx = W * H
+
+    host = torch.empty((n, 4), dtype=torch.int32, pin_memory=True)
+    wl["gen"](n, host)
+    pts = host.to(dev)
+    stream = torch.cuda.current_stream()
+    img_basic = torch.empty(npx, dtype=torch.int32, device=dev)
+    img_hq = torch.empty(npx, dtype=torch.int32, device=dev)
+    fb = pcr.pcr_create_framebuffer(W, H, pcr.PCR_FB_HQ)
+    eps = (1, 100)
+
+    names = ["raster_atomicmin", "resolve_basic", "hq_accumulate", "resolve_hq"]
+
+    def frame(evs=None):
+        def mark(i):
+            if evs is not None:
+                evs[i].record(stream)
+        mark(0)
+        pcr.pcr_render_atomicmin(fb, pts, view, stream)
+        mark(1)
+        pcr.pcr_resolve_basic(fb, img_basic, 0, False, stream)
+        mark(2)
+        pcr.pcr_hq_accumulate(fb, pts, view, *eps, stream)
+        mark(3)
+        pcr.pcr_resolve(fb, img_hq, 0, True, stream)
+        mark(4)
+
+    # roofline probes: measured random u64 atomic rate at this framebuffer size, streaming read rate
+    ceil = ctypes.CDLL(pcr_build.build_ceilings())
+    ceil.pcr_ceiling_random_atomics.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32,
+                                                ctypes.c_void_p]
+    ceil.pcr_ceiling_stream_read.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]
+    slots = torch.full((npx,), -1, dtype=torch.int64, device=dev)
+    sink = torch.empty(torch.cuda.get_device_properties(dev).multi_processor_count * 64 * 256, dtype=torch.int32,
+                       device=dev)
+    n_ops = 1 << 28
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            best = min(best, a.elapsed_time(b))
+        return best
+
+    s_ptr = ctypes.c_void_p(stream.cuda_stream)
+    t_at = timed(lambda: ceil.pcr_ceiling_random_atomics(ctypes.c_void_p(slots.data_ptr()), npx, n_ops, 0, s_ptr))
+    atomic_rate = n_ops / (t_at * 1e-3)
+    t_rd = timed(lambda: ceil.pcr_ceiling_stream_read(ctypes.c_void_p(pts.data_ptr()), n,
+                                                      ctypes.c_void_p(sink.data_ptr()), s_ptr))
+    read_gbs = n * BYTES_PER_POINT / (t_rd * 1e-3) / 1e9
+    del slots
+
+    for _ in range(args.warmup):
+        frame()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = pcr.pcr_kernel_launch_count()
+    with ClockSampler(torch.cuda.current_device()) as clocks:
+        start.record(stream)
+        for k in range(args.steps):
+            frame(evs[k])
+        stop.record(stream)
+        torch.cuda.synchronize()
+    launches = pcr.pcr_kernel_launch_count() - launches0
+    if dist:
+        dist.barrier()
+    ms = start.elapsed_time(stop)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    per_kernel = {nm: sum(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps)) / args.steps
+                  for i, nm in enumerate(names)}
+    status = pcr.pcr_get_device_status(fb)
+
+    # end to end: pinned host points -> device, full frame, both images -> pinned host
+    out_basic = torch.empty(npx, dtype=torch.int32, pin_memory=True)
+    out_hq = torch.empty(npx, dtype=torch.int32, pin_memory=True)
+
+    def e2e_frame():
+        pts.copy_(host, non_blocking=True)
+        frame()
+        out_basic.copy_(img_basic, non_blocking=True)
+        out_hq.copy_(img_hq, non_blocking=True)
+
+    e2e = None
+    if not args.no_e2e:
+        for _ in range(2):
+            e2e_frame()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            e2e_frame()
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = a.elapsed_time(b) / args.steps
+        if dist:
+            t = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": world * n / (e2e_ms * 1e-3) / 1e9, "unit": "Gpts/s", "ms_per_step": e2e_ms,
+               "h2d_bytes_per_step": n * BYTES_PER_POINT, "d2h_bytes_per_step": 2 * npx * 4}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    hbm_peak, peak_kind = _peaks()
+    dominant = max(("raster_atomicmin", "hq_accumulate"), key=lambda k: per_kernel[k])
+    kernel_name = {"raster_atomicmin": "k_raster", "hq_accumulate": "k_hq"}[dominant]
+    achieved = n * BYTES_PER_POINT / (per_kernel[dominant] * 1e-3) / 1e9
+    pass1_pts = n / (per_kernel["raster_atomicmin"] * 1e-3)
+    pass2_pts = n / (per_kernel["hq_accumulate"] * 1e-3)
+    hbm_pts = hbm_peak * 1e9 / BYTES_PER_POINT
+    result = {
+        "metric": METRIC, "value": world * n / (ms_step * 1e-3) / 1e9, "unit": "Gpts/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"exact": "f32+f64", "fp64": "f64", "double-float": "f32"}[args.transform],
+        "data": "synthetic",
+        "config": {"workload": wl["desc"], "points": n, "width": W, "height": H, "transform": args.transform,
+                   "step": "atomicMin pass + basic resolve + HQ band pass + HQ resolve with clear",
+                   "l2": "inputs 1.6 GB > 129 MB L2: no flush between steps",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "kernels_ms": per_kernel,
+        "atomicmin_gpts": pass1_pts / 1e9,
+        "hq_splat_gpts": n / ((per_kernel["raster_atomicmin"] + per_kernel["hq_accumulate"] +
+                                per_kernel["resolve_hq"]) * 1e-3) / 1e9,
+        "roofline": {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "peak_kind": peak_kind,
+                     "traffic": _traffic(kernel_name, args.workload, n)},
+        "atomic_roofline": {
+            "random_u64_atomics_per_s": atomic_rate, "stream_read_gbs": read_gbs,
+            "atomicmin_frac_of_min_hbm_atomic": pass1_pts / min(hbm_pts, atomic_rate),
+            "hq_accumulate_frac_of_min_hbm_atomic": pass2_pts / min(hbm_pts, atomic_rate / 2)},
+        "clocks": clocks.summary(),
+        "gpu_launches": launches,
+        "device_status": status,
+    }
+    if e2e:
+        result["e2e"] = e2e
+    if not args.no_cpu_baseline and world == 1:
+        sample_n = min(n, args.cpu_sample)
+        sample = host[:sample_n].numpy().view(np.uint32)
+        t = cpu_oracle_frame(sample, view)
+        result["cpu_baseline"] = {"value": sample_n / t / 1e9, "unit": "Gpts/s", "cores": 1, "kind": "oracle",
+                                  "sample": f"first {sample_n} points of the workload, one full frame "
+                                            f"(both passes and resolves), {t:.1f} s"}
+    print(json.dumps(result), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="lidar100m")
+    ap.add_argument("--transform", choices=["exact", "fp64", "double-float"], default="exact")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=100_000_000)
+    ap.add_argument("--reference-sample", type=int, default=20_000_000)
+    args = ap.parse_args()
+    wl = _workload(args.workload)
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    main()

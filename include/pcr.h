@@ -1,0 +1,178 @@
+/* pcr.h - C ABI of libpcr, a point-cloud rasterizer for NVIDIA GB300 (sm_103a).
+ *
+ * Method: Schuetz & Wimmer, "Rendering Point Clouds with Compute Shaders" (arXiv 1908.02681).
+ *   Section 2.1 (Rasterization via AtomicMin): every point is projected, its depth is computed in double
+ *   precision and turned into a 40-bit integer, the integer is shifted left by 24 bits and OR-ed with
+ *   the point's 24-bit RGB, and a 64-bit atomicMin writes the key into a per-pixel u64 framebuffer; a
+ *   per-pixel pass then turns keys into colours and clears the framebuffer.
+ *   Section 2.2 (High-Quality Splatting): a depth pass as above, a second pass that sums R, G, B and a
+ *   fragment count over the fragments whose linear depth is at most 1 % larger than the pixel's
+ *   closest depth, and a resolve that divides the sums by the count.
+ *
+ * Conventions used by every entry point
+ *   - Points: pcr_point, 16 bytes (float32 x, y, z; RGBA8 word with byte 0 = R), array of structures,
+ *     in device memory owned by the caller, 16-byte aligned.
+ *   - Framebuffers: opaque, device memory owned by the library, one per pcr_create_framebuffer call,
+ *     on the device that was current at creation. Row-major, row 0 = bottom (OpenGL NDC orientation).
+ *     Key layout: (depth code << 24) | (rgba & 0xFFFFFF). Empty pixel = 0xFFFFFFFFFFFFFFFF.
+ *   - Streams: pcr_stream_t is a cudaStream_t (NULL = legacy default stream). Render, clear and resolve
+ *     calls only enqueue work on that stream and return; argument errors are reported synchronously
+ *     and enqueue nothing. Calls on one framebuffer from different streams must be ordered by the caller.
+ *   - Errors: every call returns a pcr_status; PCR_OK is 0. A failed call leaves a message for the
+ *     calling thread in pcr_last_error_message(). No C++ exception crosses this interface and no kernel
+ *     traps: conditions found on the device (HQ count overflow) set a status word that
+ *     pcr_get_device_status() reports.
+ *   - Thread safety: distinct framebuffers may be used from distinct host threads concurrently.
+ */
+#ifndef PCR_H_
+#define PCR_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PCR_OK = 0,
+  PCR_ERR_INVALID_ARG = 1, /* bad pointer, size, alignment, view or flag; nothing was enqueued */
+  PCR_ERR_CUDA = 2,        /* a CUDA runtime call or launch failed; see pcr_last_error_message() */
+  PCR_ERR_OOM = 3,         /* device allocation failed */
+  PCR_ERR_OVERFLOW = 4,    /* HQ: some pixel received more than 2^24 contributing fragments */
+  PCR_ERR_TIMEOUT = 5      /* a bounded device-side wait gave up */
+} pcr_status;
+
+typedef void* pcr_stream_t; /* a cudaStream_t */
+
+typedef struct pcr_framebuffer pcr_framebuffer;
+
+/* One point: 16 bytes. rgba byte 0 = R, 1 = G, 2 = B, 3 = A (alpha is not used). */
+typedef struct {
+  float x, y, z;
+  uint32_t rgba;
+} pcr_point;
+
+/* Depth-code mappings (Section 2.1: "uniform or customizable" precision).
+ *   LINEAR:    q = floor((w - near) * s), s = 2^40 / (far - near), both operations rounded in FP64.
+ *   METRIC:    q = floor(w * metric_scale) (the paper's example: metres * 1000 = millimetres).
+ *   PIECEWISE: sub-ranges [lo_k, hi_k) at res_k codes per metre, codes of range k following those of
+ *              range k-1: q = base_k + floor((w - lo_k) * res_k), base_k = sum_{j<k} ceil((hi_j - lo_j) * res_j);
+ *              depths outside every range are culled (Section 2.1's nm / um / mm example).
+ * In every mode q = min(q, 2^40 - 2), so that no key equals the empty value. */
+enum { PCR_DEPTH_LINEAR = 0, PCR_DEPTH_METRIC = 1, PCR_DEPTH_PIECEWISE = 2 };
+
+/* How the per-point transform is evaluated.
+ *   EXACT: the result of the FP64 definition, bit for bit (default). The library evaluates most points
+ *          in single-precision arithmetic whose error bound proves the FP64 result, and sends the
+ *          points that the bound cannot decide through FP64.
+ *   FP64:  every point through the FP64 operations directly (same output as EXACT, slower).
+ *   DOUBLE_FLOAT: single-precision pair ("double-float") arithmetic without the FP64 arbiter; output may
+ *          differ from the FP64 definition in rare depth codes or pixels (precision study only). */
+enum { PCR_TRANSFORM_EXACT = 0, PCR_TRANSFORM_FP64 = 1, PCR_TRANSFORM_DOUBLE_FLOAT = 2 };
+
+#define PCR_MAX_DEPTH_RANGES 8
+
+/* A camera. For each point (X, Y, Z) = (double)(x, y, z):
+ *   clip_r = fma(M[r][2], Z, fma(M[r][1], Y, fma(M[r][0], X, M[r][3]))) for r = 0 (cx), 1 (cy), 3 (w);
+ *   culled unless near <= w < far (NaN culled);
+ *   fx = fmaf((float)cx / (float)w, 0.5f, 0.5f) * (float)W, same for fy with cy and H (IEEE single);
+ *   culled unless 0 <= fx < W and 0 <= fy < H; pixel = (int)fy * W + (int)fx.
+ * Requirements: every matrix entry finite; 0 < near < far < inf; metric_scale > 0 and finite for METRIC;
+ * 1 <= n_ranges <= 8 ascending non-overlapping ranges with 0 <= lo < hi, res > 0 for PIECEWISE. */
+typedef struct {
+  double view_proj[16]; /* row-major 4x4, clip = M * (x, y, z, 1) (OpenGL perspective * lookAt) */
+  double near_plane;
+  double far_plane;
+  int32_t depth_mode;   /* PCR_DEPTH_* */
+  int32_t transform;    /* PCR_TRANSFORM_* */
+  double metric_scale;  /* METRIC: codes per metre (1000.0 = millimetres) */
+  int32_t n_ranges;     /* PIECEWISE: number of used rows of `ranges` */
+  int32_t reserved;     /* must be 0 */
+  double ranges[PCR_MAX_DEPTH_RANGES][3]; /* PIECEWISE: {lo (m), hi (m), codes per metre} */
+} pcr_view;
+
+/* Framebuffer flags. */
+#define PCR_FB_HQ 1u /* also allocate the 16 B/pixel HQ accumulation buffer (needed by pcr_render_hq_splat) */
+
+/* Allocates a width x height framebuffer on the current device (keys: 8 B/pixel; with PCR_FB_HQ also
+ * sums: 16 B/pixel) and clears it (synchronously). width, height in 1..16384. */
+pcr_status pcr_create_framebuffer(int32_t width, int32_t height, uint32_t flags, pcr_framebuffer** out);
+
+/* Frees the framebuffer (synchronises the device first). NULL is accepted. */
+pcr_status pcr_destroy_framebuffer(pcr_framebuffer* fb);
+
+/* Size and flags of a framebuffer. Any output pointer may be NULL. */
+pcr_status pcr_framebuffer_info(const pcr_framebuffer* fb, int32_t* width, int32_t* height, uint32_t* flags);
+
+/* Section 2.1 (clear value): keys to 0xFFFFFFFFFFFFFFFF and, for HQ framebuffers, sums and counts to 0. */
+pcr_status pcr_clear(pcr_framebuffer* fb, pcr_stream_t stream);
+
+/* Section 2.1: rasterizes n points into fb with one 64-bit atomic minimum per visible fragment (keys
+ * accumulate with what fb holds; call pcr_clear or resolve with clear_after to start a frame).
+ * n == 0 is a no-op; n < 2^40. */
+pcr_status pcr_render_atomicmin(pcr_framebuffer* fb, const pcr_point* d_points, uint64_t n, const pcr_view* view,
+                                pcr_stream_t stream);
+
+/* pcr_render_atomicmin that also adds, to d_counts[0..3] (caller-owned device u64, not cleared), how the
+ * EXACT transform's single-precision evaluation classified the points: [0] depth code proven, [1] code
+ * undecided between two neighbours, [2] of those, sent to the FP64 arbiter because they could still win
+ * their pixel, [3] cull or pixel undecided (sent to the FP64 arbiter). All four stay 0 when the view is
+ * evaluated by the FP64 kernels (transform FP64, piecewise depth, or a view outside the single-precision
+ * preconditions). A diagnostic for the precision of the transform; the framebuffer result is the same. */
+pcr_status pcr_render_atomicmin_stats(pcr_framebuffer* fb, const pcr_point* d_points, uint64_t n,
+                                      const pcr_view* view, uint64_t* d_counts, pcr_stream_t stream);
+
+/* Section 2.2: high-quality splatting of n points into an HQ framebuffer: pass 1 = pcr_render_atomicmin;
+ * pass 2 adds (R, G, B, 1) of every fragment with eps_den * (q - qmin) <= eps_num * (qmin + Nq) to its
+ * pixel's sums, where qmin = key >> 24 after pass 1 and Nq = floor(near * s) (LINEAR) or 0 (METRIC), i.e.
+ * linear depth at most (1 + eps_num / eps_den) times the closest (eps = 1/100 in the paper).
+ * Requirements: fb created with PCR_FB_HQ, and cleared; depth_mode LINEAR or METRIC; 1 <= eps_den <= 2^20;
+ * eps_num * (2^40 + Nq) < 2^64. Colour sums are u32 per channel: valid while every pixel gets at most 2^24
+ * contributing fragments (checked by the HQ resolve, reported as PCR_ERR_OVERFLOW). */
+pcr_status pcr_render_hq_splat(pcr_framebuffer* fb, const pcr_point* d_points, uint64_t n, const pcr_view* view,
+                               uint32_t eps_num, uint32_t eps_den, pcr_stream_t stream);
+
+/* Section 2.2, second pass only: the band accumulation of pcr_render_hq_splat, for a framebuffer whose
+ * keys already hold pass 1 of the same points and view (pcr_render_atomicmin). Same requirements as
+ * pcr_render_hq_splat; pcr_render_hq_splat == pcr_render_atomicmin followed by this call. */
+pcr_status pcr_hq_accumulate(pcr_framebuffer* fb, const pcr_point* d_points, uint64_t n, const pcr_view* view,
+                             uint32_t eps_num, uint32_t eps_den, pcr_stream_t stream);
+
+/* Section 2.1 (second shader) / Section 2.2 (third pass): writes one RGBA8 word per pixel into
+ * d_rgba_out (caller-owned device memory, width * height u32, row 0 = bottom). For a framebuffer without
+ * PCR_FB_HQ: the key's colour with alpha 255, background_rgba where empty. With PCR_FB_HQ: per channel
+ * (sum + count / 2) / count with alpha 255, background_rgba where count == 0. clear_after != 0 also
+ * clears the framebuffer (as the paper's resolve shader does). */
+pcr_status pcr_resolve(pcr_framebuffer* fb, uint32_t* d_rgba_out, uint32_t background_rgba, int32_t clear_after,
+                       pcr_stream_t stream);
+
+/* Section 2.1 resolve of the keys of any framebuffer (the basic image of an HQ frame, whose pass 1 holds
+ * it). clear_after != 0 clears keys (and HQ sums). */
+pcr_status pcr_resolve_basic(pcr_framebuffer* fb, uint32_t* d_rgba_out, uint32_t background_rgba,
+                             int32_t clear_after, pcr_stream_t stream);
+
+/* Read-only device pointers to the key buffer (width * height u64) and, for HQ framebuffers, the sums
+ * (width * height pairs of u64: {R | G << 32, B | count << 32}); *d_accum = NULL otherwise. Valid until
+ * pcr_destroy_framebuffer. Either output pointer may be NULL. */
+pcr_status pcr_framebuffer_keys(const pcr_framebuffer* fb, const uint64_t** d_keys, const uint64_t** d_accum);
+
+/* Synchronises `stream`, then returns and resets the device-side status of fb: PCR_ERR_OVERFLOW if an
+ * HQ resolve found a pixel with more than 2^24 fragments, PCR_ERR_TIMEOUT if a bounded wait gave up,
+ * else PCR_OK. */
+pcr_status pcr_get_device_status(pcr_framebuffer* fb, pcr_stream_t stream);
+
+/* Number of kernels this library has launched in this process (all devices, all streams). Lets a caller
+ * check how many GPU launches a region of its own code made. */
+uint64_t pcr_kernel_launch_count(void);
+
+/* Static description of a status code. */
+const char* pcr_status_string(pcr_status status);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char* pcr_last_error_message(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PCR_H_ */

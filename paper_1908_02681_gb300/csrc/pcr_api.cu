@@ -1,0 +1,368 @@
+// libpcr host side: the C ABI declared in include/pcr.h (argument checks, per-view constants,
+// framebuffer ownership, launches).
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "pcr.h"
+#include "pcr_certified.cuh"
+#include "pcr_kernels.cuh"
+
+struct pcr_framebuffer {
+  int32_t width, height;
+  uint32_t flags;
+  int device;
+  unsigned long long* keys;  // width * height
+  ulonglong2* accum;         // width * height (HQ only)
+  uint32_t* status;          // device status word
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+std::atomic<uint64_t> g_launches{0};
+
+pcr_status fail(pcr_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+pcr_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(PCR_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+// Streaming multiprocessor count of a device (cached per device id).
+int sm_count(int device) {
+  static std::mutex mu;
+  static int cache[64] = {0};
+  std::lock_guard<std::mutex> lock(mu);
+  if (device < 0 || device >= 64) return 1;
+  if (cache[device] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || v <= 0) v = 1;
+    cache[device] = v;
+  }
+  return cache[device];
+}
+
+// Blocks for a grid-stride kernel: enough to fill every SM `per_sm` times, no more than the work needs.
+unsigned grid_for(uint64_t work_items, int threads, int device, int per_sm) {
+  const uint64_t need = (work_items + threads - 1) / threads;
+  const uint64_t cap = (uint64_t)sm_count(device) * per_sm;
+  const uint64_t g = need < cap ? need : cap;
+  return (unsigned)(g > 0 ? g : 1);
+}
+
+bool finite(double x) { return std::isfinite(x); }
+
+// Validates a view and fills the device constants. Error text goes to the thread's last error.
+pcr_status make_dev_view(const pcr_view* view, int32_t width, int32_t height, pcr::DevView* dv) {
+  if (!view) return fail(PCR_ERR_INVALID_ARG, "view is NULL");
+  for (int i = 0; i < 16; ++i)
+    if (!finite(view->view_proj[i])) return fail(PCR_ERR_INVALID_ARG, "view_proj[%d] is not finite", i);
+  const double near_ = view->near_plane, far_ = view->far_plane;
+  if (!(near_ > 0.0) || !(far_ > near_) || !finite(far_))
+    return fail(PCR_ERR_INVALID_ARG, "need 0 < near < far < inf (near=%g far=%g)", near_, far_);
+  if (view->transform < PCR_TRANSFORM_EXACT || view->transform > PCR_TRANSFORM_DOUBLE_FLOAT)
+    return fail(PCR_ERR_INVALID_ARG, "unknown transform %d", view->transform);
+  if (view->reserved != 0) return fail(PCR_ERR_INVALID_ARG, "reserved field must be 0");
+  std::memset(dv, 0, sizeof(*dv));
+  const int rows[3] = {0, 1, 3};
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 4; ++c) dv->m[4 * r + c] = view->view_proj[4 * rows[r] + c];
+  dv->near_ = near_;
+  dv->far_ = far_;
+  dv->depth_mode = view->depth_mode;
+  dv->width = width;
+  dv->height = height;
+  dv->fwidth = (float)width;
+  dv->fheight = (float)height;
+  switch (view->depth_mode) {
+    case PCR_DEPTH_LINEAR:
+      dv->scale = 1099511627776.0 / (far_ - near_);  // 2^40 / (far - near), FP64
+      dv->nq = (unsigned long long)std::floor(near_ * dv->scale);
+      break;
+    case PCR_DEPTH_METRIC:
+      if (!(view->metric_scale > 0.0) || !finite(view->metric_scale))
+        return fail(PCR_ERR_INVALID_ARG, "metric_scale must be positive and finite");
+      dv->scale = view->metric_scale;
+      dv->nq = 0;
+      break;
+    case PCR_DEPTH_PIECEWISE: {
+      if (view->n_ranges < 1 || view->n_ranges > PCR_MAX_DEPTH_RANGES)
+        return fail(PCR_ERR_INVALID_ARG, "n_ranges must be in 1..%d", PCR_MAX_DEPTH_RANGES);
+      double base = 0.0;
+      for (int k = 0; k < view->n_ranges; ++k) {
+        const double lo = view->ranges[k][0], hi = view->ranges[k][1], res = view->ranges[k][2];
+        if (!(lo >= 0.0) || !(hi > lo) || !finite(hi) || !(res > 0.0) || !finite(res))
+          return fail(PCR_ERR_INVALID_ARG, "range %d invalid (need 0 <= lo < hi, res > 0)", k);
+        if (k > 0 && lo < view->ranges[k - 1][1]) return fail(PCR_ERR_INVALID_ARG, "ranges overlap at %d", k);
+        dv->lo[k] = lo;
+        dv->hi[k] = hi;
+        dv->res[k] = res;
+        dv->base[k] = base;
+        base += std::ceil((hi - lo) * res);
+      }
+      if (!(base < 9007199254740992.0)) return fail(PCR_ERR_INVALID_ARG, "piecewise ranges exceed 2^53 codes");
+      dv->n_ranges = view->n_ranges;
+      break;
+    }
+    default:
+      return fail(PCR_ERR_INVALID_ARG, "unknown depth_mode %d", view->depth_mode);
+  }
+  return PCR_OK;
+}
+
+pcr_status check_fb(const pcr_framebuffer* fb) {
+  if (!fb) return fail(PCR_ERR_INVALID_ARG, "framebuffer is NULL");
+  return PCR_OK;
+}
+
+pcr_status check_points(const pcr_point* d_points, uint64_t n) {
+  if (n == 0) return PCR_OK;
+  if (!d_points) return fail(PCR_ERR_INVALID_ARG, "d_points is NULL");
+  if (reinterpret_cast<uintptr_t>(d_points) & 15u) return fail(PCR_ERR_INVALID_ARG, "d_points is not 16-byte aligned");
+  if (n >= (1ull << 40)) return fail(PCR_ERR_INVALID_ARG, "n must be below 2^40");
+  return PCR_OK;
+}
+
+pcr_status after_launch(const char* what, uint64_t launches = 1) {
+  g_launches.fetch_add(launches, std::memory_order_relaxed);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? PCR_OK : cuda_fail(e, what);
+}
+
+// Launches pass 1 (atomic minimum) for a validated view.
+pcr_status launch_raster(pcr_framebuffer* fb, const pcr_point* d_points, uint64_t n, const pcr::DevView& dv,
+                         int transform, cudaStream_t s, unsigned long long* stats = nullptr) {
+  const uint4* pts = reinterpret_cast<const uint4*>(d_points);
+  if (transform == PCR_TRANSFORM_FP64) {
+    pcr::k_raster_fp64<<<grid_for(n, 256, fb->device, 8), 256, 0, s>>>(pts, n, dv, fb->keys);
+    return after_launch("k_raster_fp64");
+  }
+  return pcr::launch_raster_certified(pts, n, dv, transform == PCR_TRANSFORM_DOUBLE_FLOAT, fb->keys,
+                                      sm_count(fb->device), s, stats)
+             ? after_launch("k_raster_certified")
+             : fail(PCR_ERR_CUDA, "certified raster launch failed");
+}
+
+pcr_status launch_hq(pcr_framebuffer* fb, const pcr_point* d_points, uint64_t n, const pcr::DevView& dv,
+                     int transform, uint32_t eps_num, uint32_t eps_den, cudaStream_t s) {
+  const uint4* pts = reinterpret_cast<const uint4*>(d_points);
+  unsigned long long* acc = reinterpret_cast<unsigned long long*>(fb->accum);
+  if (transform == PCR_TRANSFORM_FP64) {
+    pcr::k_hq_fp64<<<grid_for(n, 256, fb->device, 8), 256, 0, s>>>(pts, n, dv, fb->keys, acc, eps_num, eps_den);
+    return after_launch("k_hq_fp64");
+  }
+  return pcr::launch_hq_certified(pts, n, dv, transform == PCR_TRANSFORM_DOUBLE_FLOAT, fb->keys, acc, eps_num,
+                                  eps_den, sm_count(fb->device), s)
+             ? after_launch("k_hq_certified")
+             : fail(PCR_ERR_CUDA, "certified HQ launch failed");
+}
+
+}  // namespace
+
+extern "C" {
+
+pcr_status pcr_create_framebuffer(int32_t width, int32_t height, uint32_t flags, pcr_framebuffer** out) {
+  if (!out) return fail(PCR_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (width < 1 || width > 16384 || height < 1 || height > 16384)
+    return fail(PCR_ERR_INVALID_ARG, "width and height must be in 1..16384 (got %d x %d)", width, height);
+  if (flags & ~PCR_FB_HQ) return fail(PCR_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
+  pcr_framebuffer* fb = new (std::nothrow) pcr_framebuffer();
+  if (!fb) return fail(PCR_ERR_OOM, "host allocation failed");
+  fb->width = width;
+  fb->height = height;
+  fb->flags = flags;
+  cudaError_t e = cudaGetDevice(&fb->device);
+  if (e != cudaSuccess) {
+    delete fb;
+    return cuda_fail(e, "cudaGetDevice");
+  }
+  const uint64_t npx = (uint64_t)width * (uint64_t)height;
+  e = cudaMalloc(&fb->keys, npx * sizeof(unsigned long long));
+  if (e == cudaSuccess && (flags & PCR_FB_HQ)) e = cudaMalloc(&fb->accum, npx * sizeof(ulonglong2));
+  if (e == cudaSuccess) e = cudaMalloc(&fb->status, 256);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(fb->keys);
+    cudaFree(fb->accum);
+    cudaFree(fb->status);
+    delete fb;
+    return e == cudaErrorMemoryAllocation ? fail(PCR_ERR_OOM, "cudaMalloc of %llu pixels failed", (unsigned long long)npx)
+                                          : cuda_fail(e, "cudaMalloc");
+  }
+  e = cudaMemset(fb->status, 0, 256);
+  if (e == cudaSuccess) {
+    pcr::k_clear<<<grid_for(npx / 2 + 1, 256, fb->device, 4), 256>>>(fb->keys, fb->accum, npx);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    pcr_destroy_framebuffer(fb);
+    return cuda_fail(e, "framebuffer clear");
+  }
+  *out = fb;
+  return PCR_OK;
+}
+
+pcr_status pcr_destroy_framebuffer(pcr_framebuffer* fb) {
+  if (!fb) return PCR_OK;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(fb->device);
+  cudaDeviceSynchronize();
+  cudaFree(fb->keys);
+  cudaFree(fb->accum);
+  cudaFree(fb->status);
+  cudaSetDevice(prev);
+  delete fb;
+  return PCR_OK;
+}
+
+pcr_status pcr_framebuffer_info(const pcr_framebuffer* fb, int32_t* width, int32_t* height, uint32_t* flags) {
+  if (pcr_status st = check_fb(fb)) return st;
+  if (width) *width = fb->width;
+  if (height) *height = fb->height;
+  if (flags) *flags = fb->flags;
+  return PCR_OK;
+}
+
+pcr_status pcr_clear(pcr_framebuffer* fb, pcr_stream_t stream) {
+  if (pcr_status st = check_fb(fb)) return st;
+  const uint64_t npx = (uint64_t)fb->width * fb->height;
+  pcr::k_clear<<<grid_for(npx / 2 + 1, 256, fb->device, 4), 256, 0, (cudaStream_t)stream>>>(fb->keys, fb->accum, npx);
+  return after_launch("k_clear");
+}
+
+pcr_status pcr_render_atomicmin(pcr_framebuffer* fb, const pcr_point* d_points, uint64_t n, const pcr_view* view,
+                                pcr_stream_t stream) {
+  if (pcr_status st = check_fb(fb)) return st;
+  if (pcr_status st = check_points(d_points, n)) return st;
+  pcr::DevView dv;
+  if (pcr_status st = make_dev_view(view, fb->width, fb->height, &dv)) return st;
+  if (n == 0) return PCR_OK;
+  return launch_raster(fb, d_points, n, dv, view->transform, (cudaStream_t)stream);
+}
+
+pcr_status pcr_render_atomicmin_stats(pcr_framebuffer* fb, const pcr_point* d_points, uint64_t n,
+                                      const pcr_view* view, uint64_t* d_counts, pcr_stream_t stream) {
+  if (pcr_status st = check_fb(fb)) return st;
+  if (pcr_status st = check_points(d_points, n)) return st;
+  if (!d_counts || (reinterpret_cast<uintptr_t>(d_counts) & 7u)) return fail(PCR_ERR_INVALID_ARG, "d_counts invalid");
+  pcr::DevView dv;
+  if (pcr_status st = make_dev_view(view, fb->width, fb->height, &dv)) return st;
+  if (n == 0) return PCR_OK;
+  return launch_raster(fb, d_points, n, dv, view->transform, (cudaStream_t)stream,
+                       reinterpret_cast<unsigned long long*>(d_counts));
+}
+
+namespace {
+
+// Checks shared by the two HQ entry points; fills dv.
+pcr_status check_hq(pcr_framebuffer* fb, const pcr_point* d_points, uint64_t n, const pcr_view* view, uint32_t eps_num,
+                    uint32_t eps_den, pcr::DevView* dv) {
+  if (pcr_status st = check_fb(fb)) return st;
+  if (!(fb->flags & PCR_FB_HQ)) return fail(PCR_ERR_INVALID_ARG, "framebuffer was created without PCR_FB_HQ");
+  if (pcr_status st = check_points(d_points, n)) return st;
+  if (pcr_status st = make_dev_view(view, fb->width, fb->height, dv)) return st;
+  if (dv->depth_mode == PCR_DEPTH_PIECEWISE)
+    return fail(PCR_ERR_INVALID_ARG, "HQ splatting needs codes proportional to depth (LINEAR or METRIC)");
+  if (eps_den == 0 || eps_den > (1u << 20)) return fail(PCR_ERR_INVALID_ARG, "eps_den must be in 1..2^20");
+  // eps_num * (qmin + Nq) must not wrap for any qmin < 2^40
+  const long double lim = (long double)eps_num * ((long double)(1ull << 40) + (long double)dv->nq);
+  if (lim >= 18446744073709551616.0L) return fail(PCR_ERR_INVALID_ARG, "eps_num * (2^40 + Nq) must be below 2^64");
+  return PCR_OK;
+}
+
+}  // namespace
+
+pcr_status pcr_render_hq_splat(pcr_framebuffer* fb, const pcr_point* d_points, uint64_t n, const pcr_view* view,
+                               uint32_t eps_num, uint32_t eps_den, pcr_stream_t stream) {
+  pcr::DevView dv;
+  if (pcr_status st = check_hq(fb, d_points, n, view, eps_num, eps_den, &dv)) return st;
+  if (n == 0) return PCR_OK;
+  const cudaStream_t s = (cudaStream_t)stream;
+  if (pcr_status st = launch_raster(fb, d_points, n, dv, view->transform, s)) return st;
+  return launch_hq(fb, d_points, n, dv, view->transform, eps_num, eps_den, s);
+}
+
+pcr_status pcr_hq_accumulate(pcr_framebuffer* fb, const pcr_point* d_points, uint64_t n, const pcr_view* view,
+                             uint32_t eps_num, uint32_t eps_den, pcr_stream_t stream) {
+  pcr::DevView dv;
+  if (pcr_status st = check_hq(fb, d_points, n, view, eps_num, eps_den, &dv)) return st;
+  if (n == 0) return PCR_OK;
+  return launch_hq(fb, d_points, n, dv, view->transform, eps_num, eps_den, (cudaStream_t)stream);
+}
+
+pcr_status pcr_resolve(pcr_framebuffer* fb, uint32_t* d_rgba_out, uint32_t background_rgba, int32_t clear_after,
+                       pcr_stream_t stream) {
+  if (pcr_status st = check_fb(fb)) return st;
+  if (!d_rgba_out) return fail(PCR_ERR_INVALID_ARG, "d_rgba_out is NULL");
+  if (!(fb->flags & PCR_FB_HQ)) return pcr_resolve_basic(fb, d_rgba_out, background_rgba, clear_after, stream);
+  const uint64_t npx = (uint64_t)fb->width * fb->height;
+  pcr::k_resolve_hq<<<grid_for(npx, 256, fb->device, 4), 256, 0, (cudaStream_t)stream>>>(
+      fb->accum, fb->keys, d_rgba_out, npx, background_rgba, clear_after != 0, fb->status);
+  return after_launch("k_resolve_hq");
+}
+
+pcr_status pcr_resolve_basic(pcr_framebuffer* fb, uint32_t* d_rgba_out, uint32_t background_rgba,
+                             int32_t clear_after, pcr_stream_t stream) {
+  if (pcr_status st = check_fb(fb)) return st;
+  if (!d_rgba_out) return fail(PCR_ERR_INVALID_ARG, "d_rgba_out is NULL");
+  const uint64_t npx = (uint64_t)fb->width * fb->height;
+  pcr::k_resolve_basic<<<grid_for(npx, 256, fb->device, 4), 256, 0, (cudaStream_t)stream>>>(
+      fb->keys, fb->accum, d_rgba_out, npx, background_rgba, clear_after != 0);
+  return after_launch("k_resolve_basic");
+}
+
+pcr_status pcr_framebuffer_keys(const pcr_framebuffer* fb, const uint64_t** d_keys, const uint64_t** d_accum) {
+  if (pcr_status st = check_fb(fb)) return st;
+  if (d_keys) *d_keys = reinterpret_cast<const uint64_t*>(fb->keys);
+  if (d_accum) *d_accum = reinterpret_cast<const uint64_t*>(fb->accum);
+  return PCR_OK;
+}
+
+pcr_status pcr_get_device_status(pcr_framebuffer* fb, pcr_stream_t stream) {
+  if (pcr_status st = check_fb(fb)) return st;
+  const cudaStream_t s = (cudaStream_t)stream;
+  uint32_t word = 0;
+  cudaError_t e = cudaMemcpyAsync(&word, fb->status, sizeof(word), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(fb->status, 0, sizeof(word), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "reading the device status");
+  if (word & pcr::kStatusOverflow)
+    return fail(PCR_ERR_OVERFLOW, "an HQ pixel received more than 2^24 contributing fragments");
+  if (word & pcr::kStatusTimeout) return fail(PCR_ERR_TIMEOUT, "a bounded device-side wait gave up");
+  return PCR_OK;
+}
+
+const char* pcr_status_string(pcr_status status) {
+  switch (status) {
+    case PCR_OK: return "PCR_OK";
+    case PCR_ERR_INVALID_ARG: return "PCR_ERR_INVALID_ARG: invalid argument";
+    case PCR_ERR_CUDA: return "PCR_ERR_CUDA: CUDA runtime error";
+    case PCR_ERR_OOM: return "PCR_ERR_OOM: device allocation failed";
+    case PCR_ERR_OVERFLOW: return "PCR_ERR_OVERFLOW: HQ fragment count above 2^24 in a pixel";
+    case PCR_ERR_TIMEOUT: return "PCR_ERR_TIMEOUT: bounded device wait expired";
+  }
+  return "unknown pcr_status";
+}
+
+const char* pcr_last_error_message(void) { return g_last_error.c_str(); }
+
+uint64_t pcr_kernel_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"

@@ -1,0 +1,70 @@
+"""The C ABI library loads and exports every entry point that include/*.h declares; host-side argument
+checks reject bad input before any CUDA call (no GPU needed)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_1908_02681_gb300 import build as pcr_build
+from paper_1908_02681_gb300 import pcr
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b(pcr_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pcr_build.build()
+    return pcr.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    ceil = ctypes.CDLL(pcr_build.build_ceilings())
+    names = _declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        target = ceil if n.startswith("pcr_ceiling_") else lib
+        assert hasattr(target, n), n
+    assert pcr.pcr_kernel_launch_count() == 0   # nothing launched without a GPU
+
+
+def test_status_strings(lib):
+    for s in range(6):
+        assert pcr.pcr_status_string(s).startswith("PCR_")
+    assert "unknown" in pcr.pcr_status_string(99)
+
+
+def test_host_argument_checks(lib):
+    out = ctypes.c_void_p()
+    assert lib.pcr_create_framebuffer(0, 10, 0, ctypes.byref(out)) == pcr.PCR_ERR_INVALID_ARG
+    assert "width and height" in pcr.pcr_last_error_message()
+    assert lib.pcr_create_framebuffer(16385, 10, 0, ctypes.byref(out)) == pcr.PCR_ERR_INVALID_ARG
+    assert lib.pcr_create_framebuffer(10, 10, 0x80, ctypes.byref(out)) == pcr.PCR_ERR_INVALID_ARG
+    assert lib.pcr_create_framebuffer(10, 10, 0, None) == pcr.PCR_ERR_INVALID_ARG
+    v = pcr.pcr_view()
+    assert lib.pcr_render_atomicmin(None, None, 0, ctypes.byref(v), None) == pcr.PCR_ERR_INVALID_ARG
+    assert lib.pcr_clear(None, None) == pcr.PCR_ERR_INVALID_ARG
+    assert lib.pcr_resolve(None, None, 0, 0, None) == pcr.PCR_ERR_INVALID_ARG
+    assert lib.pcr_get_device_status(None, None) == pcr.PCR_ERR_INVALID_ARG
+    assert lib.pcr_destroy_framebuffer(None) == pcr.PCR_OK
+
+
+def test_view_marshalling():
+    from tests.helpers import axis_view
+    v = axis_view(depth_mode=2)
+    v.ranges = [[0.0, 10.0, 1e9], [10.0, 1e4, 1e6]]
+    c = pcr.make_view(v)
+    assert c.n_ranges == 2 and c.ranges[1][2] == 1e6 and c.depth_mode == 2
+    assert c.view_proj[14] == -1.0 and c.near_plane == 0.5
+    assert ctypes.sizeof(pcr.pcr_view) == 16 * 8 + 2 * 8 + 2 * 4 + 8 + 2 * 4 + 8 * 3 * 8

@@ -1,0 +1,177 @@
+"""GPU vs oracle parity through the C ABI (bit-exact keys, exact HQ sums, resolved RGB).
+
+Tolerances: keys and HQ sums/counts are integers and must match exactly; resolved RGBA is integer
+arithmetic on those sums and must match exactly as well (the +-1 LSB allowance for HQ colours is not
+needed because both sides divide the same integers with the same rounding).
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+from tests.helpers import RawView, axis_view, pack, rgba
+
+pytestmark = pytest.mark.gpu
+
+TRANSFORMS = [0, 1]  # PCR_TRANSFORM_EXACT, PCR_TRANSFORM_FP64 (both must equal the FP64 definition)
+
+
+def _dev(points):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(points).view(np.int32)).cuda()
+
+
+def _with_transform(view, transform):
+    v = RawView(np.asarray(view.view_proj), view.near, view.far, view.width, view.height,
+                getattr(view, "depth_mode", 0), getattr(view, "metric_scale", 1000.0), getattr(view, "ranges", None),
+                transform)
+    return v
+
+
+def _render_basic(pcr, pts_dev, view):
+    fb = pcr.pcr_create_framebuffer(view.width, view.height)
+    pcr.pcr_render_atomicmin(fb, pts_dev, view)
+    keys, _ = pcr.pcr_framebuffer_keys(fb)
+    out = pcr.keys_to_numpy(keys)
+    return fb, out
+
+
+def _compare_basic(pcr, points, view, transform):
+    v = _with_transform(view, transform)
+    fb, got = _render_basic(pcr, _dev(points), v)
+    ref = oracle.render_atomicmin(points, view)
+    mism = np.flatnonzero(got != ref)
+    assert mism.size == 0, f"{mism.size} pixels differ, first {mism[:5]}: got {got[mism[:3]]} want {ref[mism[:3]]}"
+    import torch
+    img = torch.empty(view.width * view.height, dtype=torch.int32, device="cuda")
+    pcr.pcr_resolve(fb, img, background_rgba=0x00203040)
+    assert np.array_equal(img.cpu().numpy().view(np.uint32), oracle.resolve_basic(ref, 0x00203040))
+    return ref
+
+
+@pytest.mark.parametrize("transform", TRANSFORMS)
+def test_cube_1m_640x480(gpu, transform):
+    """1M uniform unit-cube points, 640x480, fov 60, near 0.1, far 10, linear 40-bit depth."""
+    pts = scenes.cube(1_000_000, 1)
+    ref = _compare_basic(gpu, pts, scenes.cube_1m_view(), transform)
+    assert np.count_nonzero(ref != oracle.EMPTY) > 20000
+
+
+@pytest.mark.parametrize("transform", TRANSFORMS)
+def test_lidar_ragged_1080p_basic_and_hq(gpu, transform):
+    """LIDAR scene, 3M + 7 points (ragged tail), 1920x1080, basic and HQ (eps = 1 %)."""
+    import torch
+    pts = scenes.lidar(3_000_007, 2)
+    view = scenes.lidar_1km_view()
+    v = _with_transform(view, transform)
+    dev = _dev(pts)
+    fb = gpu.pcr_create_framebuffer(view.width, view.height, gpu.PCR_FB_HQ)
+    gpu.pcr_render_hq_splat(fb, dev, v, 1, 100)
+    keys, acc = gpu.pcr_framebuffer_keys(fb)
+    got_keys = gpu.keys_to_numpy(keys)
+    got_acc = acc.cpu().numpy().view(np.uint64)
+    ref = oracle.render_atomicmin(pts, view)
+    assert np.array_equal(got_keys, ref), np.count_nonzero(got_keys != ref)
+    (sr, sg, sb, cnt), ovf = oracle.hq_accumulate(pts, view, ref, 1, 100)
+    assert not ovf
+    assert np.array_equal(got_acc[:, 0] & 0xFFFFFFFF, sr)
+    assert np.array_equal(got_acc[:, 0] >> 32, sg)
+    assert np.array_equal(got_acc[:, 1] & 0xFFFFFFFF, sb)
+    assert np.array_equal(got_acc[:, 1] >> 32, cnt)
+    img = torch.empty(view.pixels if hasattr(view, "pixels") else view.width * view.height, dtype=torch.int32,
+                      device="cuda")
+    gpu.pcr_resolve_basic(fb, img, 0)
+    assert np.array_equal(img.cpu().numpy().view(np.uint32), oracle.resolve_basic(ref))
+    gpu.pcr_resolve(fb, img, 0x01020304, clear_after=True)
+    assert np.array_equal(img.cpu().numpy().view(np.uint32), oracle.resolve_hq((sr, sg, sb, cnt), 0x01020304))
+    assert gpu.pcr_get_device_status(fb) == gpu.PCR_OK
+    # clear_after left an empty framebuffer
+    keys, acc = gpu.pcr_framebuffer_keys(fb)
+    assert bool((keys == -1).all()) and bool((acc == 0).all())
+
+
+@pytest.mark.parametrize("transform", TRANSFORMS)
+def test_hand_built_edges(gpu, transform):
+    """Frustum edges, clip planes, NaN/Inf, ties and identical points (the oracle pins' scenes)."""
+    c = rgba(1, 2, 3)
+    view = axis_view(64, 48, near=0.5, far=8.5)
+    pts = pack([[-2.0, -2.0, -2.0], [2.0, 0.0, -2.0], [0.0, 2.0, -2.0], [0.0, 0.0, -0.5], [0.0, 0.0, -8.5],
+                [0.0, 0.0, 1.0], [float("nan"), 0.0, -1.0], [float("inf"), 0.0, -1.0], [0.0, 0.0, float("-inf")],
+                [0.5, 0.5, -1.0], [0.5, 0.5, -1.0], [0.5, 0.5, -1.0]],
+               [c] * 9 + [rgba(0, 0, 1), rgba(255, 0, 0), rgba(0, 0, 1)])
+    _compare_basic(gpu, pts, view, transform)
+
+
+@pytest.mark.parametrize("transform", TRANSFORMS)
+@pytest.mark.parametrize("n", [0, 1, 31, 33, 257, 4099])
+def test_small_and_ragged_counts(gpu, transform, n):
+    pts = scenes.cube(n, 100 + n) if n else np.zeros((0, 4), np.uint32)
+    view = scenes.View.lookat((0.2, 0.1, 1.6), (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), 70.0, 33, 17, 0.1, 10.0)
+    _compare_basic(gpu, pts, view, transform)
+
+
+@pytest.mark.parametrize("transform", TRANSFORMS)
+def test_metric_and_piecewise_modes(gpu, transform):
+    pts = scenes.lidar(500_000, 4)
+    base = scenes.lidar_1km_view(640, 360)
+    mview = RawView(base.view_proj, base.near, base.far, 640, 360, depth_mode=1, metric_scale=1000.0)
+    _compare_basic(gpu, pts, mview, transform)
+    pview = RawView(base.view_proj, base.near, base.far, 640, 360, depth_mode=2,
+                    ranges=np.array([[0.0, 10.0, 1e9], [10.0, 1e4, 1e6], [1e4, 1e7, 1e3]]))
+    _compare_basic(gpu, pts, pview, transform)
+
+
+@pytest.mark.parametrize("transform", TRANSFORMS)
+def test_maximum_dimensions(gpu, transform):
+    pts = scenes.cube(20000, 7)
+    for w, h in ((16384, 1), (1, 16384), (4096, 3)):
+        view = scenes.View.lookat((0.0, 0.0, 2.0), (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), 60.0, w, h, 0.1, 10.0)
+        _compare_basic(gpu, pts, view, transform)
+
+
+def test_order_invariance(gpu):
+    pts = scenes.lidar(2_000_000, 6)
+    view = scenes.lidar_1km_view()
+    _, a = _render_basic(gpu, _dev(pts), view)
+    sh = scenes.shuffle(pts.copy(), 3)
+    _, b = _render_basic(gpu, _dev(sh), view)
+    assert np.array_equal(a, b)
+
+
+def test_accumulate_clear_and_errors(gpu):
+    import torch
+    pts = scenes.cube(100_000, 9)
+    view = scenes.cube_1m_view()
+    dev = _dev(pts)
+    fb = gpu.pcr_create_framebuffer(view.width, view.height)
+    gpu.pcr_render_atomicmin(fb, dev[:50_000], view)
+    gpu.pcr_render_atomicmin(fb, dev[50_000:], view)
+    keys, _ = gpu.pcr_framebuffer_keys(fb)
+    assert np.array_equal(gpu.keys_to_numpy(keys), oracle.render_atomicmin(pts, view))
+    gpu.pcr_clear(fb)
+    torch.cuda.synchronize()
+    assert bool((keys == -1).all())
+    with pytest.raises(gpu.PcrError):
+        gpu.pcr_render_atomicmin(fb, dev[1:].view(-1)[1:4 * 1000 + 1].view(1000, 4), view)  # misaligned
+    with pytest.raises(gpu.PcrError):
+        gpu.pcr_render_hq_splat(fb, dev, view)          # framebuffer without PCR_FB_HQ
+    bad = RawView(view.view_proj, 1.0, 0.5, view.width, view.height)
+    with pytest.raises(gpu.PcrError):
+        gpu.pcr_render_atomicmin(fb, dev, bad)
+
+
+def test_hq_overflow_reported(gpu):
+    """More than 2^24 contributing fragments in one pixel: the HQ resolve reports PCR_ERR_OVERFLOW."""
+    import torch
+    n = (1 << 24) + 5
+    view = axis_view(4, 4, near=0.5, far=8.5)
+    one = pack([[0.0, 0.0, -1.0]], [rgba(255, 255, 255)])
+    dev = _dev(one).expand(n, 4).contiguous()
+    fb = gpu.pcr_create_framebuffer(4, 4, gpu.PCR_FB_HQ)
+    gpu.pcr_render_hq_splat(fb, dev, view)
+    img = torch.empty(16, dtype=torch.int32, device="cuda")
+    gpu.pcr_resolve(fb, img)
+    assert gpu.pcr_get_device_status(fb) == gpu.PCR_ERR_OVERFLOW
+    assert gpu.pcr_get_device_status(fb) == gpu.PCR_OK     # status was reset
