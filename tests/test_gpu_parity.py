@@ -175,3 +175,85 @@ def test_hq_overflow_reported(gpu):
     gpu.pcr_resolve(fb, img)
     assert gpu.pcr_get_device_status(fb) == gpu.PCR_ERR_OVERFLOW
     assert gpu.pcr_get_device_status(fb) == gpu.PCR_OK     # status was reset
+
+
+def _near_boundary_points(view, n_candidates, seed):
+    """Points inside the view whose depth value t, pixel coordinate fx or clip x lies very close to a
+    decision boundary of the definition (an integer code, a pixel edge, a float rounding midpoint), found
+    by evaluating the transform in numpy FP64 (without fma; within ~1e-12 relative of the definition)."""
+    rng = np.random.default_rng(seed)
+    M = np.asarray(view.view_proj, dtype=np.float64)
+    # random points in front of the camera: sample ndc and depth, map back through the inverse matrix
+    inv = np.linalg.inv(M)
+    ndc = rng.uniform(-1.0, 1.0, (n_candidates, 2))
+    w = view.near + (min(view.far, 2000.0) - view.near) * rng.uniform(0.0, 1.0, n_candidates) ** 2
+    # clip z of an OpenGL perspective matrix at depth w: (f + n) / (f - n) * w + 2 f n / (n - f)
+    f_, n_ = view.far, view.near
+    zc = (f_ + n_) / (f_ - n_) * w + 2.0 * f_ * n_ / (n_ - f_)
+    clip = np.stack([ndc[:, 0] * w, ndc[:, 1] * w, zc, w], 1)
+    world = clip @ inv.T
+    world = world[:, :3] / world[:, 3:4]
+    xyz = world.astype(np.float32)
+    P = np.concatenate([xyz.astype(np.float64), np.ones((n_candidates, 1))], 1)
+    cx, cy, ww = P @ M[0], P @ M[1], P @ M[3]
+    s = 2.0 ** 40 / (view.far - view.near)
+    t = (ww - view.near) * s
+    ft = t - np.floor(t)
+    fx = (cx.astype(np.float32) / ww.astype(np.float32) * 0.5 + 0.5) * view.width
+    ffx = fx - np.floor(fx)
+    c32 = cx.astype(np.float32).astype(np.float64)
+    ulp = np.abs(np.spacing(cx.astype(np.float32))).astype(np.float64)
+    mid = np.abs(np.abs(cx - c32) - ulp / 2) / np.maximum(ulp, 1e-300)
+    sel = (np.minimum(ft, 1 - ft) < 2e-3) | (np.minimum(ffx, 1 - ffx) < 1e-4) | (mid < 1e-4)
+    cols = rng.integers(0, 1 << 32, n_candidates, dtype=np.uint64).astype(np.uint32)
+    return pack(xyz[sel], cols[sel]), int(sel.sum())
+
+
+@pytest.mark.parametrize("transform", TRANSFORMS)
+def test_adversarial_near_boundaries(gpu, transform):
+    """Points selected to sit next to code, pixel-edge and float-rounding boundaries: rendered alone
+    (no occlusion to hide a wrong candidate) and mixed into a scene."""
+    view = scenes.lidar_1km_view(640, 360)
+    pts, n_sel = _near_boundary_points(view, 3_000_000, 5)
+    assert n_sel > 5000
+    _compare_basic(gpu, pts, view, transform)
+    mixed = np.concatenate([scenes.lidar(500_000, 8), pts])
+    _compare_basic(gpu, mixed, view, transform)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_views(gpu, seed):
+    """Random cameras (eye, target, fov, near/far ratio from 20 to 1e7, resolution, depth mode) on the
+    LIDAR scene and a large cube: the certified transform must equal the definition bit for bit."""
+    rng = np.random.default_rng(1000 + seed)
+    big = seed % 2 == 0
+    pts = scenes.lidar(300_000, 30 + seed) if big else scenes.cube(300_000, 30 + seed, half=0.5 * 10.0 ** rng.uniform(-2, 3))
+    centre = np.array([500.0, 500.0, 0.0]) if big else np.zeros(3)
+    scale = 700.0 if big else float(np.abs(pts[:, :3].view(np.float32)).max()) * 3
+    eye = centre + rng.normal(0, 1, 3) * scale
+    target = centre + rng.normal(0, 0.2, 3) * scale
+    d = float(np.linalg.norm(eye - centre)) + scale
+    near = d * 10.0 ** rng.uniform(-5, -1)
+    far = d * 10.0 ** rng.uniform(0.3, 2)
+    w, h = int(rng.integers(16, 2000)), int(rng.integers(16, 1200))
+    view = scenes.View.lookat(eye, target, (0.0, 0.0, 1.0) if big else (0.0, 1.0, 0.0), float(rng.uniform(20, 110)),
+                              w, h, near, far)
+    if seed % 3 == 1:
+        view.depth_mode, view.metric_scale = 1, float(10.0 ** rng.uniform(0, 6))
+    _compare_basic(gpu, pts, view, 0)
+
+
+def test_certified_classification_rates(gpu):
+    """Most points are decided in single precision; report the shares (for the design notes)."""
+    import torch
+    pts = scenes.lidar(3_000_000, 2)
+    view = scenes.lidar_1km_view()
+    fb = gpu.pcr_create_framebuffer(view.width, view.height)
+    counts = torch.zeros(4, dtype=torch.int64, device="cuda")
+    gpu.pcr_render_atomicmin_stats(fb, _dev(pts), view, counts)
+    exact, amb, amb_fp64, hard = (int(c) for c in counts.cpu())
+    keys, _ = gpu.pcr_framebuffer_keys(fb)
+    assert np.array_equal(gpu.keys_to_numpy(keys), oracle.render_atomicmin(pts, view))
+    print(f"\ncertified: exact {exact}, ambiguous {amb} (arbiter {amb_fp64}), hard {hard} of {len(pts)}")
+    assert exact > 0.9 * (exact + amb + hard)
+    assert amb_fp64 + hard < 0.01 * len(pts)
