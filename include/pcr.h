@@ -91,6 +91,13 @@ typedef struct {
   double ranges[PCR_MAX_DEPTH_RANGES][3]; /* PIECEWISE: {lo (m), hi (m), codes per metre} */
 } pcr_view;
 
+/* Launch tuning of a framebuffer's point passes (the knobs an autotuner sets). Results never depend on it. */
+typedef struct {
+  int32_t merge_same_pixel; /* 1: the fragments of one warp that land on the same pixel are merged with warp
+                               reductions, then one atomic per pixel; 0 (default): one atomic per fragment */
+  int32_t blocks_per_sm;    /* 256-thread blocks per SM for the point passes, 1..32 (default 8) */
+} pcr_tuning;
+
 /* Framebuffer flags. */
 #define PCR_FB_HQ 1u /* also allocate the 16 B/pixel HQ accumulation buffer (needed by pcr_render_hq_splat) */
 
@@ -100,6 +107,21 @@ pcr_status pcr_create_framebuffer(int32_t width, int32_t height, uint32_t flags,
 
 /* Frees the framebuffer (synchronises the device first). NULL is accepted. */
 pcr_status pcr_destroy_framebuffer(pcr_framebuffer* fb);
+
+/* Sets the launch tuning used by later render calls on fb (NULL restores the defaults). Not ordered with
+ * work already enqueued; calls racing with a render call on another thread are the caller's to avoid. */
+pcr_status pcr_set_tuning(pcr_framebuffer* fb, const pcr_tuning* tuning);
+
+/* Current launch tuning of fb. */
+pcr_status pcr_get_tuning(const pcr_framebuffer* fb, pcr_tuning* tuning);
+
+/* Autotuner: renders one frame of (d_points, n, view) on fb for every candidate tuning (same-pixel merging
+ * on and off, 2 / 4 / 6 / 8 blocks per SM), times the point passes with CUDA events on `stream` (pass 1,
+ * plus pass 2 with eps 1/100 for HQ framebuffers; best of two runs), and keeps the fastest in fb. Writes it
+ * to *best when best is not NULL. Clears fb before every run and at the end; synchronises `stream`.
+ * Arguments as for pcr_render_atomicmin; n must be > 0. */
+pcr_status pcr_autotune(pcr_framebuffer* fb, const pcr_point* d_points, uint64_t n, const pcr_view* view,
+                        pcr_stream_t stream, pcr_tuning* best);
 
 /* Size and flags of a framebuffer. Any output pointer may be NULL. */
 pcr_status pcr_framebuffer_info(const pcr_framebuffer* fb, int32_t* width, int32_t* height, uint32_t* flags);
@@ -114,11 +136,12 @@ pcr_status pcr_render_atomicmin(pcr_framebuffer* fb, const pcr_point* d_points, 
                                 pcr_stream_t stream);
 
 /* pcr_render_atomicmin that also adds, to d_counts[0..3] (caller-owned device u64, not cleared), how the
- * EXACT transform's single-precision evaluation classified the points: [0] depth code proven, [1] code
- * undecided between two neighbours, [2] of those, sent to the FP64 arbiter because they could still win
- * their pixel, [3] cull or pixel undecided (sent to the FP64 arbiter). All four stay 0 when the view is
- * evaluated by the FP64 kernels (transform FP64, piecewise depth, or a view outside the single-precision
- * preconditions). A diagnostic for the precision of the transform; the framebuffer result is the same. */
+ * EXACT transform's single-precision evaluation handled the points: [0] decided by the first tier (float
+ * pixel estimate with its error bound, exact depth code), [1] depth code undecided between two
+ * neighbours, [2] sent to the FP64 arbiter, [3] deferred to the second tier (double-float clip values).
+ * All four stay 0 when the view is evaluated by the FP64 kernels (transform FP64, piecewise depth, or a
+ * view outside the single-precision preconditions). A diagnostic of the transform; the framebuffer
+ * result is the same as pcr_render_atomicmin's. */
 pcr_status pcr_render_atomicmin_stats(pcr_framebuffer* fb, const pcr_point* d_points, uint64_t n,
                                       const pcr_view* view, uint64_t* d_counts, pcr_stream_t stream);
 

@@ -19,6 +19,7 @@ struct pcr_framebuffer {
   unsigned long long* keys;  // width * height
   ulonglong2* accum;         // width * height (HQ only)
   uint32_t* status;          // device status word
+  pcr::Tuning tuning;        // launch tuning of the point passes
 };
 
 namespace {
@@ -150,7 +151,7 @@ pcr_status launch_raster(pcr_framebuffer* fb, const pcr_point* d_points, uint64_
     return after_launch("k_raster_fp64");
   }
   return pcr::launch_raster_certified(pts, n, dv, transform == PCR_TRANSFORM_DOUBLE_FLOAT, fb->keys,
-                                      sm_count(fb->device), s, stats)
+                                      sm_count(fb->device), s, stats, fb->tuning)
              ? after_launch("k_raster_certified")
              : fail(PCR_ERR_CUDA, "certified raster launch failed");
 }
@@ -164,7 +165,7 @@ pcr_status launch_hq(pcr_framebuffer* fb, const pcr_point* d_points, uint64_t n,
     return after_launch("k_hq_fp64");
   }
   return pcr::launch_hq_certified(pts, n, dv, transform == PCR_TRANSFORM_DOUBLE_FLOAT, fb->keys, acc, eps_num,
-                                  eps_den, sm_count(fb->device), s)
+                                  eps_den, sm_count(fb->device), s, fb->tuning)
              ? after_launch("k_hq_certified")
              : fail(PCR_ERR_CUDA, "certified HQ launch failed");
 }
@@ -229,6 +230,84 @@ pcr_status pcr_destroy_framebuffer(pcr_framebuffer* fb) {
   cudaSetDevice(prev);
   delete fb;
   return PCR_OK;
+}
+
+pcr_status pcr_set_tuning(pcr_framebuffer* fb, const pcr_tuning* tuning) {
+  if (pcr_status st = check_fb(fb)) return st;
+  if (!tuning) {
+    fb->tuning = pcr::Tuning();
+    return PCR_OK;
+  }
+  if (tuning->merge_same_pixel != 0 && tuning->merge_same_pixel != 1)
+    return fail(PCR_ERR_INVALID_ARG, "merge_same_pixel must be 0 or 1");
+  if (tuning->blocks_per_sm < 1 || tuning->blocks_per_sm > 32) return fail(PCR_ERR_INVALID_ARG, "blocks_per_sm must be in 1..32");
+  fb->tuning.merge = tuning->merge_same_pixel;
+  fb->tuning.blocks_per_sm = tuning->blocks_per_sm;
+  return PCR_OK;
+}
+
+pcr_status pcr_get_tuning(const pcr_framebuffer* fb, pcr_tuning* tuning) {
+  if (pcr_status st = check_fb(fb)) return st;
+  if (!tuning) return fail(PCR_ERR_INVALID_ARG, "tuning is NULL");
+  tuning->merge_same_pixel = fb->tuning.merge;
+  tuning->blocks_per_sm = fb->tuning.blocks_per_sm;
+  return PCR_OK;
+}
+
+pcr_status pcr_autotune(pcr_framebuffer* fb, const pcr_point* d_points, uint64_t n, const pcr_view* view,
+                        pcr_stream_t stream, pcr_tuning* best) {
+  if (pcr_status st = check_fb(fb)) return st;
+  if (pcr_status st = check_points(d_points, n)) return st;
+  if (n == 0) return fail(PCR_ERR_INVALID_ARG, "autotuning needs points");
+  pcr::DevView dv;
+  if (pcr_status st = make_dev_view(view, fb->width, fb->height, &dv)) return st;
+  const bool hq = (fb->flags & PCR_FB_HQ) && dv.depth_mode != PCR_DEPTH_PIECEWISE;
+  const cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(PCR_ERR_CUDA, "cudaEventCreate failed");
+  }
+  const pcr::Tuning saved = fb->tuning;
+  pcr::Tuning best_t = saved;
+  float best_ms = 3.0e38f;
+  pcr_status st = PCR_OK;
+  for (int merge = 0; merge <= 1 && st == PCR_OK; ++merge) {
+    for (int b : {2, 4, 6, 8}) {
+      fb->tuning.merge = merge;
+      fb->tuning.blocks_per_sm = b;
+      float run_best = 3.0e38f;
+      for (int rep = 0; rep < 2 && st == PCR_OK; ++rep) {
+        if ((st = pcr_clear(fb, stream)) != PCR_OK) break;
+        cudaEventRecord(e0, s);
+        st = launch_raster(fb, d_points, n, dv, view->transform, s);
+        if (st == PCR_OK && hq) st = launch_hq(fb, d_points, n, dv, view->transform, 1, 100, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "autotune timing");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        run_best = ms < run_best ? ms : run_best;
+      }
+      if (st != PCR_OK) break;
+      if (run_best < best_ms) {
+        best_ms = run_best;
+        best_t = fb->tuning;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  fb->tuning = st == PCR_OK ? best_t : saved;
+  if (st == PCR_OK) st = pcr_clear(fb, stream);
+  if (st == PCR_OK) {
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_fail(e, "autotune");
+  }
+  if (st == PCR_OK && best) {
+    best->merge_same_pixel = fb->tuning.merge;
+    best->blocks_per_sm = fb->tuning.blocks_per_sm;
+  }
+  return st;
 }
 
 pcr_status pcr_framebuffer_info(const pcr_framebuffer* fb, int32_t* width, int32_t* height, uint32_t* flags) {

@@ -20,10 +20,18 @@
 //     to is known exactly, and the single-precision pixel mapping is then evaluated with the same IEEE
 //     operations as the definition.
 //
+// The pixel is decided in two tiers. Tier 1 evaluates clip x, y, w with plain float fma chains and
+// bounds, per point, how far the definition's pixel coordinate fx can be from the float estimate (the
+// rounding of the matrix to float, the fma roundings, the definition's own float roundings, the
+// approximate reciprocal); when fx and that bound stay inside one pixel, the pixel is known. Points that
+// tier 1 cannot decide are queued per warp in shared memory and, 32 at a time, go through tier 2: the
+// double-float clip values above, whose float roundings are certified, and the definition's IEEE single
+// pixel mapping.
+//
 // A point whose depth code is undecided between two neighbours is sent on only when it could still win
 // its pixel (its smaller candidate key is below the key the framebuffer holds); a point whose cull or
-// pixel is undecided, and those, go through the FP64 definition directly (the arbiter). The output is
-// therefore bit-identical to the FP64 definition.
+// pixel tier 2 cannot decide, and those, go through the FP64 definition directly (the arbiter). The
+// output is therefore bit-identical to the FP64 definition.
 #pragma once
 
 #include <cmath>
@@ -47,8 +55,17 @@ struct CertParams {
   float t_c1, t_c2;                   // FP64-rounding + fixed-point bound of t: t_c1 * T_t + t_c2
   float Af[3], Bf;                    // float approximations of A_j and B (for T_t)
   uint32_t B0, B1, B2;                // B * 2^40 as a 96-bit two's-complement integer (low word first)
+  unsigned long long BL;              // tier 1: B * 2^40 = BH * 2^32 + BL, 0 <= BL < 2^32
+  long long BH;
   int32_t e_max[3];                   // largest biased exponent of x, y, z with a usable table entry
   long long qn_safe, qn_cull, qf_safe, qf_cull;  // depth-cull thresholds in code space
+  // tier 1: t bound from the float w-row magnitude, D = d_k1 * T_w + d_k2; pixel bound constants
+  float d_k1, d_k2;
+  float delta_c;                      // |float(clip) - fma-chain estimate| <= delta_c * T (per row)
+  float ex_a1, ex_a2, ey_a1, ey_a2;   // E = a1 |ndc| + a2 rho + 4.2u |f| + 2^-20 per axis
+  float near_in, far_in;              // w - dw > near_in => w >= near; w + dw < far_in => w < far (FP64 w)
+  float near_out, far_out;            // w + dw < near_out => w < near; w - dw > far_out => w >= far
+  float xyz_max;                      // |coordinate| below this: table entries usable, value finite
   // approximate (double-float, no arbiter) mode
   float near_h, near_l, far_h, far_l, S_h, S_l;
   int32_t approximate;
@@ -146,6 +163,8 @@ inline bool prepare_cert(const DevView& v, bool approximate, CertParams* P) {
   P->B0 = (uint32_t)bu;
   P->B1 = (uint32_t)(bu >> 32);
   P->B2 = (uint32_t)(bu >> 64);
+  P->BL = (unsigned long long)(uint32_t)bu;
+  P->BH = (long long)(b >> 32);  // arithmetic: b = BH * 2^32 + BL
   const double bd = S * m3[3] - (P->linear ? S * v.near_ : 0.0);
   if (!(std::fabs(bd) < 1e38)) return false;
   P->Bf = (float)bd;
@@ -154,6 +173,29 @@ inline bool prepare_cert(const DevView& v, bool approximate, CertParams* P) {
   const double u64 = 0x1p-53;
   P->t_c1 = (float)(5.2 * u64 * (1.0 + 0x1p-18));
   P->t_c2 = (float)((P->linear ? 3.1 * u64 * S * v.near_ : 0.0) + 0x1p-13);
+  // tier 1: T_t <= S (1 + u) T_w + S near (LINEAR), with T_w the float fma-chain magnitude of the w row
+  // (>= (1 - 3u) times the exact one): D = c1 (S (1 + 8u) T_w + S near) + c2
+  const double uf = 0x1p-24;
+  P->d_k1 = (float)(5.2 * u64 * S * (1.0 + 8.0 * uf) * (1.0 + 0x1p-18));
+  P->d_k2 = (float)(5.2 * u64 * (P->linear ? S * v.near_ : 0.0) + (double)P->t_c2);
+  // |RN32(clip_FP64) - fma-chain estimate| <= (u + 4u + 3 u64) T_H, T_H <= (1 + 3u) T_computed
+  P->delta_c = (float)(5.1 * uf);
+  // fx bound: W/2 (7u |ndc| + 1.01 rho)(1 + 5u) + 4.2u |fx| (see classify_fast)
+  P->ex_a1 = (float)(3.52 * uf * v.fwidth);
+  P->ex_a2 = (float)(0.506 * v.fwidth);
+  P->ey_a1 = (float)(3.52 * uf * v.fheight);
+  P->ey_a2 = (float)(0.506 * v.fheight);
+  // float clip-plane thresholds with (1 +- 4u) margins for the rounding of w -+ dw
+  P->near_in = std::nextafter((float)(v.near_ * (1.0 + 4.0 * uf)), 3.0e38f);
+  P->far_in = std::nextafter((float)(v.far_ * (1.0 - 4.0 * uf)), 0.0f);
+  P->near_out = std::nextafter((float)(v.near_ * (1.0 - 4.0 * uf)), 0.0f);
+  P->far_out = std::nextafter((float)(v.far_ * (1.0 + 4.0 * uf)), 3.0e38f);
+  {
+    int emin = 254;
+    for (int j = 0; j < 3; ++j) emin = P->e_max[j] < emin ? P->e_max[j] : emin;
+    P->xyz_max = std::ldexp(1.0f, emin - 127 + 1 > 127 ? 127 : emin - 127 + 1);  // 2^(e+1): exponent <= e
+    if (emin >= 254) P->xyz_max = 3.0e38f;
+  }
   // depth-cull thresholds: T_n, T_f are the FP64 codes of the near and far planes (monotone rounding:
   // t > T_n => w >= near, t < T_n => w < near, t < T_f => w < far, t > T_f => w >= far)
   const double Tn = P->linear ? 0.0 : v.near_ * S;
@@ -170,7 +212,7 @@ inline bool prepare_cert(const DevView& v, bool approximate, CertParams* P) {
 
 // ---------------------------------------------------------------------------------------------- device
 
-enum : uint32_t { kCulled = 0, kExact = 1, kAmbiguous = 2, kHard = 3 };
+enum : uint32_t { kCulled = 0, kExact = 1, kAmbiguous = 2, kHard = 3, kDefer = 4 };
 
 struct CertFrag {
   uint32_t state;
@@ -226,7 +268,44 @@ __device__ __forceinline__ void mac96(uint32_t m, long long F, uint32_t& a0, uin
       : "r"((uint32_t)p0), "r"((uint32_t)(p0 >> 32)), "r"((uint32_t)p1), "r"((uint32_t)((unsigned long long)p1 >> 32)));
 }
 
-// Classifies one point. F points at the block's shared-memory copy of P.F.
+// Depth row: floor of the fixed-point t (qc) and the top 23 fraction bits as a float in [0, 1).
+__device__ __forceinline__ void t_row(const CertParams& P, const long long* __restrict__ F, uint32_t bx, uint32_t by,
+                                      uint32_t bz, long long* qc, float* frac) {
+  uint32_t a0 = P.B0, a1 = P.B1, a2 = P.B2;
+  // a subnormal coordinate takes the implicit bit too; its table entry uses exponent 1's scale, so the
+  // product is A * (X + 2^-126 sign(X)): an error below |A| 2^-126, far inside the bound
+  mac96((bx & 0x7FFFFFu) | 0x800000u, F[(bx >> 23)], a0, a1, a2);
+  mac96((by & 0x7FFFFFu) | 0x800000u, F[kTableEntries + (by >> 23)], a0, a1, a2);
+  mac96((bz & 0x7FFFFFu) | 0x800000u, F[2 * kTableEntries + (bz >> 23)], a0, a1, a2);
+  *qc = (long long)(int32_t)a2 * 16777216LL + (long long)(a1 >> 8);  // floor(t)
+  *frac = __fsub_rn(__uint_as_float(0x3F800000u | (__funnelshift_r(a0, a1, 8) >> 9)), 1.0f);
+}
+
+// From the fixed-point t and its error bound D: the candidate codes [qa, qb] (qb = qa or qa + 1) and the
+// clip-plane decision. Returns kCulled, kHard, or kExact / kAmbiguous (visible by depth).
+__device__ __forceinline__ uint32_t depth_decision(const CertParams& P, long long qc, float frac, float D,
+                                                   long long* qa_out) {
+  if (D >= 0.5f) return kHard;
+  long long qa, qb;
+  bool exact;
+  if (frac > D && frac < __fsub_rn(1.0f, D)) {
+    qa = qb = qc;
+    exact = true;
+  } else {
+    qa = frac < 0.5f ? qc - 1 : qc;
+    qb = qa + 1;
+    exact = false;
+  }
+  if (qb <= P.qn_cull || qa >= P.qf_cull) return kCulled;  // culled by the clip planes
+  if (qa < P.qn_safe || qb > P.qf_safe) return kHard;
+  const long long qmax = (long long)kQMax;
+  if (qa >= qmax) exact = true;  // both candidates cap to 2^40 - 2
+  *qa_out = qa < qmax ? qa : qmax;
+  return exact ? kExact : kAmbiguous;
+}
+
+// Tier 2: certified double-float clip values (see the file header). F points at the block's
+// shared-memory copy of P.F.
 __device__ __forceinline__ CertFrag classify_cert(const CertParams& P, const long long* __restrict__ F, uint4 p) {
   CertFrag out{kCulled, 0u, 0};
   const uint32_t bx = p.x, by = p.y, bz = p.z;
@@ -237,38 +316,16 @@ __device__ __forceinline__ CertFrag classify_cert(const CertParams& P, const lon
     out.state = kHard;
     return out;
   }
-  // ---- depth code: t * 2^40 as a 96-bit integer
-  uint32_t a0 = P.B0, a1 = P.B1, a2 = P.B2;
-  // a subnormal coordinate takes the implicit bit too; its table entry uses exponent 1's scale, so the
-  // product is A * (X + 2^-126 sign(X)): an error below |A| 2^-126, far inside the bound
-  mac96((bx & 0x7FFFFFu) | 0x800000u, F[(bx >> 23)], a0, a1, a2);
-  mac96((by & 0x7FFFFFu) | 0x800000u, F[kTableEntries + (by >> 23)], a0, a1, a2);
-  mac96((bz & 0x7FFFFFu) | 0x800000u, F[2 * kTableEntries + (bz >> 23)], a0, a1, a2);
+  long long qc;
+  float frac;
+  t_row(P, F, bx, by, bz, &qc, &frac);
   const float x = __uint_as_float(bx), y = __uint_as_float(by), z = __uint_as_float(bz);
-  const long long qc = (long long)(int32_t)a2 * 16777216LL + (long long)(a1 >> 8);  // floor(t)
-  const float frac = __fsub_rn(__uint_as_float(0x3F800000u | (__funnelshift_r(a0, a1, 8) >> 9)), 1.0f);
   const float Tt = __fadd_rn(__fadd_rn(__fadd_rn(fabsf(__fmul_rn(P.Af[0], x)), fabsf(__fmul_rn(P.Af[1], y))),
                                        fabsf(__fmul_rn(P.Af[2], z))), fabsf(P.Bf));
   const float D = __fadd_rn(__fmaf_rn(P.t_c1, Tt, P.t_c2), 0x1p-22f);
-  long long qa, qb;
-  bool exact;
-  if (D >= 0.5f) {
-    out.state = kHard;
-    return out;
-  }
-  if (frac > D && frac < __fsub_rn(1.0f, D)) {
-    qa = qb = qc;
-    exact = true;
-  } else {
-    qa = frac < 0.5f ? qc - 1 : qc;
-    qb = qa + 1;
-    exact = false;
-  }
-  if (qb <= P.qn_cull || qa >= P.qf_cull) return out;  // culled by the clip planes
-  if (qa < P.qn_safe || qb > P.qf_safe) {
-    out.state = kHard;
-    return out;
-  }
+  long long qa = 0;
+  out.state = depth_decision(P, qc, frac, D, &qa);
+  if (out.state == kCulled || out.state == kHard) return out;
   // ---- pixel: certified float roundings of the FP64 clip values, then the definition's float ops
   bool okx, oky, okw;
   const float fw = df_row(P.H[2], P.L[2], x, y, z, P.kappa, &okw);
@@ -280,12 +337,138 @@ __device__ __forceinline__ CertFrag classify_cert(const CertParams& P, const lon
   }
   const float fx = __fmul_rn(__fmaf_rn(__fdiv_rn(fcx, fw), 0.5f, 0.5f), P.v.fwidth);
   const float fy = __fmul_rn(__fmaf_rn(__fdiv_rn(fcy, fw), 0.5f, 0.5f), P.v.fheight);
-  if (!(fx >= 0.0f && fx < P.v.fwidth && fy >= 0.0f && fy < P.v.fheight)) return out;
+  if (!(fx >= 0.0f && fx < P.v.fwidth && fy >= 0.0f && fy < P.v.fheight)) {
+    out.state = kCulled;
+    return out;
+  }
   out.pixel = (uint32_t)__float2int_rz(fy) * (uint32_t)P.v.width + (uint32_t)__float2int_rz(fx);
-  const long long qmax = (long long)kQMax;
-  if (qa >= qmax) exact = true;  // both candidates cap to 2^40 - 2
-  out.q = qa < qmax ? qa : qmax;
-  out.state = exact ? kExact : kAmbiguous;
+  out.q = qa;
+  return out;
+}
+
+// rcp.approx.ftz.f32: maximum error 1 ulp (relative 2^-23) for normal inputs.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Tier-1 pixel axis. f: float estimate of the definition's pixel coordinate; E: bound on their
+// distance; size: W or H (<= 16384). Returns 0 = inside [0, size) at pixel *px, 1 = certainly outside,
+// 2 = undecided (every comparison is written so that NaN or infinity lands here).
+__device__ __forceinline__ uint32_t pixel_axis(float f, float E, float size, uint32_t* px) {
+  if (!(E < 0.25f)) return 2u;
+  if (!(f >= 0.0f)) return f < -E ? 1u : 2u;
+  if (!(f < __fadd_rn(size, 1.0f))) return f >= __fadd_rn(size, 1.0f) ? 1u : 2u;
+  // floor via the 1.5 * 2^23 shift: for -0.5 <= f - 0.5 < 2^22 the sum lies in [2^23, 2^24), where floats
+  // are the integers, so it rounds f - 0.5 to the nearest integer: floor(f) unless f is an integer (then
+  // f - 1 or f; either way fr below falls outside [E, 1 - E) and the axis is undecided)
+  const float g = __fadd_rn(__fsub_rn(f, 0.5f), 12582912.0f);
+  const float fl = __fsub_rn(g, 12582912.0f);
+  const float fr = __fsub_rn(f, fl);  // exact: fl is an integer within 1 of f, both below 2^15
+  if (!(fr >= E && fr < __fsub_rn(1.0f, E))) return 2u;
+  const uint32_t k = (uint32_t)(__float_as_int(g) - 0x4B400000);  // bits of 1.5 * 2^23: g - 1.5 * 2^23
+  if (fl >= size) return 1u;
+  *px = k;
+  return 0u;
+}
+
+// Tier-1 result: state, pixel, and the fixed-point t as three 32-bit words (t * 2^40, low word first).
+struct FastFrag {
+  uint32_t state;  // kCulled, kExact, kAmbiguous (code qc - 1 or qc when lo_half, else qc or qc + 1), kDefer
+  uint32_t pixel;
+  uint32_t a0, a1, a2;
+  bool lo_half;    // kAmbiguous: the fraction is below one half
+};
+
+// Key of the code floor(V / 2^40) (0 <= code < 2^40 - 2): (V >> 16) with the low 24 bits replaced by RGB.
+__device__ __forceinline__ unsigned long long key_from_fixed(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t rgba) {
+  const uint32_t lo = (__funnelshift_r(a0, a1, 16) & 0xFF000000u) | (rgba & 0xFFFFFFu);
+  const uint32_t hi = __funnelshift_r(a1, a2, 16);
+  return ((unsigned long long)hi << 32) | lo;
+}
+
+__device__ __forceinline__ unsigned long long code_from_fixed(uint32_t a1, uint32_t a2) {
+  return ((unsigned long long)(a2 >> 8) << 32) | __funnelshift_r(a1, a2, 8);
+}
+
+// Tier 1: the exact depth code from the fixed-point row (two 64-bit multiply-add accumulators), the cull
+// from the float w estimate and its bound, and a float pixel estimate with a rigorous per-point bound.
+// Written without early exits: every quantity is computed for every point (a non-finite coordinate
+// only produces NaN or infinity, which every decision below treats as undecided), and the state is
+// assembled from predicates at the end.
+__device__ __forceinline__ FastFrag classify_fast(const CertParams& P, const long long* __restrict__ F, uint4 p) {
+  const float x = __uint_as_float(p.x), y = __uint_as_float(p.y), z = __uint_as_float(p.z);
+  // finite, and inside the exponent range whose table entries exist (else tier 2 decides)
+  const bool in_range = fabsf(x) < P.xyz_max && fabsf(y) < P.xyz_max && fabsf(z) < P.xyz_max;
+  // float estimates of w and its term magnitude (fma chains, as the FP64 definition orders them)
+  const float w = __fmaf_rn(P.H[2][2], z, __fmaf_rn(P.H[2][1], y, __fmaf_rn(P.H[2][0], x, P.H[2][3])));
+  const float Tw = __fmaf_rn(fabsf(P.H[2][2]), fabsf(z),
+                             __fmaf_rn(fabsf(P.H[2][1]), fabsf(y), __fmaf_rn(fabsf(P.H[2][0]), fabsf(x), fabsf(P.H[2][3]))));
+  const float dw = __fmul_rn(P.delta_c, Tw);
+  const float wlo = __fsub_rd(w, dw), whi = __fadd_ru(w, dw);  // directed: wlo <= w - dw, whi >= w + dw
+  const bool depth_out = whi < P.near_out || wlo > P.far_out;
+  const bool depth_in = wlo > P.near_in && whi < P.far_in;
+  // ---- depth code: t * 2^40 = sum m_j F_j + B, accumulated as sum m_j F_lo_j + 2^32 sum m_j F_hi_j
+  const long long fx_ = F[p.x >> 23], fy_ = F[kTableEntries + (p.y >> 23)], fz_ = F[2 * kTableEntries + (p.z >> 23)];
+  const uint32_t mx = (p.x & 0x7FFFFFu) | 0x800000u, my = (p.y & 0x7FFFFFu) | 0x800000u,
+                 mz = (p.z & 0x7FFFFFu) | 0x800000u;
+  unsigned long long L = P.BL;
+  L += (unsigned long long)mx * (uint32_t)fx_;
+  L += (unsigned long long)my * (uint32_t)fy_;
+  L += (unsigned long long)mz * (uint32_t)fz_;
+  long long Hh = P.BH;
+  Hh += (long long)(int32_t)mx * (long long)(int32_t)(fx_ >> 32);
+  Hh += (long long)(int32_t)my * (long long)(int32_t)(fy_ >> 32);
+  Hh += (long long)(int32_t)mz * (long long)(int32_t)(fz_ >> 32);
+  FastFrag out;
+  out.a0 = (uint32_t)L;
+  asm("add.cc.u32 %0, %2, %3;\n\taddc.u32 %1, %4, 0;"
+      : "=r"(out.a1), "=r"(out.a2)
+      : "r"((uint32_t)(L >> 32)), "r"((uint32_t)Hh), "r"((uint32_t)((unsigned long long)Hh >> 32)));
+  const bool code_ok = out.a2 < 0xFFFFu;  // codes in [0, 2^40 - 2^24): no cap, no sign (else tier 2)
+  const float frac =
+      __fsub_rn(__uint_as_float(0x3F800000u | (__funnelshift_r(out.a0, out.a1, 17) & 0x7FFFFFu)), 1.0f);
+  const float D = __fadd_rn(__fmaf_rn(P.d_k1, Tw, P.d_k2), 0x1p-22f);
+  const bool exact = frac > D && frac < __fsub_rn(1.0f, D);
+  out.lo_half = frac < 0.5f;
+  // an undecided code is usable (two candidates) when the bound is small and the code is not 0 or -1
+  const bool amb_ok = D < 0.25f && !(out.lo_half && out.a2 == 0u && (out.a1 >> 8) == 0u);
+  // ---- pixel estimate
+  const float cx = __fmaf_rn(P.H[0][2], z, __fmaf_rn(P.H[0][1], y, __fmaf_rn(P.H[0][0], x, P.H[0][3])));
+  const float Tx = __fmaf_rn(fabsf(P.H[0][2]), fabsf(z),
+                             __fmaf_rn(fabsf(P.H[0][1]), fabsf(y), __fmaf_rn(fabsf(P.H[0][0]), fabsf(x), fabsf(P.H[0][3]))));
+  const float cy = __fmaf_rn(P.H[1][2], z, __fmaf_rn(P.H[1][1], y, __fmaf_rn(P.H[1][0], x, P.H[1][3])));
+  const float Ty = __fmaf_rn(fabsf(P.H[1][2]), fabsf(z),
+                             __fmaf_rn(fabsf(P.H[1][1]), fabsf(y), __fmaf_rn(fabsf(P.H[1][0]), fabsf(x), fabsf(P.H[1][3]))));
+  // with wlo > near_in > 0: rcp.approx (relative error <= 2^-23); (1 + 1e-6) makes rden >= 1 / (w - dw)
+  const float rw = rcp_approx(w);
+  const float rden = __fmul_rn(rcp_approx(wlo), 1.000001f);
+  const float ndx = __fmul_rn(cx, rw), ndy = __fmul_rn(cy, rw);
+  const float fx = __fmul_rn(__fmaf_rn(ndx, 0.5f, 0.5f), P.v.fwidth);
+  const float fy = __fmul_rn(__fmaf_rn(ndy, 0.5f, 0.5f), P.v.fheight);
+  // |fx_FP64 - fx| <= E = W ((3.52u + 0.506 rho') |nd| + 0.506 rden dc T + 2.13u (|nd| + 1)) + 2^-20 with
+  // rho' = rden dw (see the file header); |fx| <= W (|nd| + 1) / 2 folds the 4.25u |fx| term
+  const float k1 = __fmaf_rn(0.506f, __fmul_rn(rden, dw), 5.65f * 0x1p-24f);
+  const float k2 = __fmul_rn(__fmul_rn(0.506f, rden), P.delta_c);
+  const float Ex = __fmaf_rn(P.v.fwidth, __fmaf_rn(k1, fabsf(ndx), __fmaf_rn(k2, Tx, 2.13f * 0x1p-24f)), 0x1p-20f);
+  const float Ey = __fmaf_rn(P.v.fheight, __fmaf_rn(k1, fabsf(ndy), __fmaf_rn(k2, Ty, 2.13f * 0x1p-24f)), 0x1p-20f);
+  // floor via the 1.5 * 2^23 shift: for -0.5 <= f - 0.5 < 2^22 the sum lies in [2^23, 2^24), where floats
+  // are the integers, so it rounds f - 0.5 to the nearest integer: floor(f) unless f is an integer (then
+  // f - 1 or f, and fr below falls outside [E, 1 - E)). Outside that range k is far above the image size.
+  const float gx = __fadd_rn(__fsub_rn(fx, 0.5f), 12582912.0f), gy = __fadd_rn(__fsub_rn(fy, 0.5f), 12582912.0f);
+  const uint32_t kx = (uint32_t)(__float_as_int(gx) - 0x4B400000), ky = (uint32_t)(__float_as_int(gy) - 0x4B400000);
+  const float frx = __fsub_rn(fx, __fsub_rn(gx, 12582912.0f)), fry = __fsub_rn(fy, __fsub_rn(gy, 12582912.0f));
+  const bool small_e = Ex < 0.25f && Ey < 0.25f;
+  const bool ax_ok = kx < (uint32_t)P.v.width && frx >= Ex && frx < __fsub_rn(1.0f, Ex) &&
+                     ky < (uint32_t)P.v.height && fry >= Ey && fry < __fsub_rn(1.0f, Ey);
+  const bool ax_out = fx < -Ex || fx >= __fadd_ru(P.v.fwidth, Ex) || fy < -Ey || fy >= __fadd_ru(P.v.fheight, Ey);
+  // ---- state
+  uint32_t st = kDefer;
+  if (in_range && (depth_out || (depth_in && small_e && ax_out))) st = kCulled;
+  else if (in_range && depth_in && small_e && ax_ok && code_ok && (exact || amb_ok)) st = exact ? kExact : kAmbiguous;
+  out.state = st;
+  out.pixel = ky * (uint32_t)P.v.width + kx;
   return out;
 }
 
@@ -339,121 +522,354 @@ __device__ __forceinline__ void load_table(const CertParams& P, long long* sF) {
   __syncthreads();
 }
 
-// Pass 1 (Section 2.1) with the certified transform. Undecided depth codes are resolved by occlusion
-// when possible; everything else undecided goes through the FP64 definition.
-template <bool kApprox>
-__global__ void __launch_bounds__(256) k_raster_cert(const uint4* __restrict__ pts, uint64_t n,
-                                                     const __grid_constant__ CertParams P,
-                                                     unsigned long long* __restrict__ keys,
-                                                     unsigned long long* __restrict__ stats) {
-  __shared__ long long sF[3 * kTableEntries];
-  if (!kApprox) load_table(P, sF);
-  unsigned c_exact = 0, c_amb = 0, c_amb_fp64 = 0, c_hard = 0;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const uint4 p = ld_stream16(pts + i);
-    const CertFrag f = kApprox ? classify_df(P, p) : classify_cert(P, sF, p);
-    if (f.state == kExact) {
-      ++c_exact;
-      atomicMin(keys + f.pixel, make_key((unsigned long long)f.q, p.w));
-      continue;
-    }
-    bool arbiter = f.state == kHard;
-    if (f.state == kAmbiguous) {
-      ++c_amb;
-      // the smaller candidate cannot win when it is not below the stored key (keys only decrease)
-      arbiter = make_key((unsigned long long)f.q, p.w) < keys[f.pixel];
-      c_amb_fp64 += arbiter;
-    } else {
-      c_hard += arbiter;
-    }
-    if (arbiter) {
-      uint32_t pix;
-      unsigned long long q;
-      if (project_fp64(P.v, __uint_as_float(p.x), __uint_as_float(p.y), __uint_as_float(p.z), &pix, &q))
-        atomicMin(keys + pix, make_key(q, p.w));
-    }
+#ifndef PCR_CERT_MIN_BLOCKS
+#define PCR_CERT_MIN_BLOCKS 8
+#endif
+// points loaded per thread before any is processed (memory-level parallelism of the streaming loop)
+#ifndef PCR_CERT_BATCH
+#define PCR_CERT_BATCH 2
+#endif
+constexpr int kBatch = PCR_CERT_BATCH;
+constexpr int kCertThreads = 256;
+constexpr int kCertWarps = kCertThreads / 32;
+constexpr int kQueue = 64;  // per-warp deferral queue (points), >= 2 * 32 - 1
+
+// Pass-1 handling of a tier-2 result: returns true when the point still has to go to the FP64 arbiter.
+__device__ __forceinline__ bool raster_commit(const CertFrag& f, uint32_t rgba, unsigned long long* keys) {
+  if (f.state == kExact) {
+    atomicMin(keys + f.pixel, make_key((unsigned long long)f.q, rgba));
+    return false;
   }
-  if (stats) {
-    atomicAdd(stats + 0, (unsigned long long)c_exact);
-    atomicAdd(stats + 1, (unsigned long long)c_amb);
-    atomicAdd(stats + 2, (unsigned long long)c_amb_fp64);
-    atomicAdd(stats + 3, (unsigned long long)c_hard);
+  if (f.state == kAmbiguous)  // the smaller candidate cannot win when not below the stored key
+    return make_key((unsigned long long)f.q, rgba) < keys[f.pixel];
+  return f.state == kHard;
+}
+
+// Tier 2 + arbiter for one deferred point (pass 1). Kept out of line: it runs for a small fraction of the
+// points, and inlining it would raise the register count of the main loop.
+__device__ __noinline__ void raster_deferred(const CertParams& P, const long long* sF, uint4 p,
+                                             unsigned long long* keys, unsigned* c_fp64) {
+  const CertFrag f = classify_cert(P, sF, p);
+  if (raster_commit(f, p.w, keys)) {
+    ++*c_fp64;
+    uint32_t pix;
+    unsigned long long q;
+    if (project_fp64(P.v, __uint_as_float(p.x), __uint_as_float(p.y), __uint_as_float(p.z), &pix, &q))
+      atomicMin(keys + pix, make_key(q, p.w));
   }
 }
 
-// Pass 2 (Section 2.2) with the certified transform.
-template <bool kApprox>
-__global__ void __launch_bounds__(256) k_hq_cert(const uint4* __restrict__ pts, uint64_t n,
-                                                 const __grid_constant__ CertParams P,
-                                                 const unsigned long long* __restrict__ keys,
-                                                 unsigned long long* __restrict__ accum, uint32_t eps_num,
-                                                 uint32_t eps_den) {
+// Commits one key per lane (has = true) with one atomic minimum per distinct pixel of the warp: lanes
+// whose fragments land on the same pixel are grouped (match.any) and their smallest key found with two
+// 32-bit warp reductions (high word, then low word among the lanes holding the smallest high word).
+// All 32 lanes must call it.
+template <bool kMerge>
+__device__ __forceinline__ void commit_min(bool has, uint32_t pix, unsigned long long key, unsigned long long* keys,
+                                           uint32_t lane) {
+  if (!kMerge) {
+    if (has) atomicMin(keys + pix, key);
+    return;
+  }
+  const unsigned act = __ballot_sync(0xFFFFFFFFu, has);
+  if (has) {
+    const unsigned grp = __match_any_sync(act, pix);
+    const unsigned hi = (unsigned)(key >> 32), lo = (unsigned)key;
+    const unsigned mhi = __reduce_min_sync(grp, hi);
+    const unsigned mlo = __reduce_min_sync(grp, hi == mhi ? lo : 0xFFFFFFFFu);
+    if ((grp & ((1u << lane) - 1u)) == 0u) atomicMin(keys + pix, ((unsigned long long)mhi << 32) | mlo);
+  }
+}
+
+// Appends the deferring lanes' points to the warp's shared-memory queue; when 32 are queued, each lane
+// takes one and runs `handle` on it (all 32 lanes converged). qn is warp-uniform.
+template <typename H>
+__device__ __forceinline__ void defer_points(bool defer, const uint4& p, uint4* q, uint32_t& qn, uint32_t lane,
+                                             H&& handle) {
+  const unsigned m = __ballot_sync(0xFFFFFFFFu, defer);
+  if (m == 0u) return;
+  if (defer) q[qn + __popc(m & ((1u << lane) - 1u))] = p;
+  qn += __popc(m);
+  __syncwarp();
+  if (qn >= 32u) {
+    qn -= 32u;
+    const uint4 d = q[qn + lane];
+    __syncwarp();
+    handle(d);
+  }
+}
+
+// Pass 1 (Section 2.1) with the certified transform. Tier 1 handles nearly every point; the others are
+// queued per warp in shared memory and handled 32 at a time by tier 2 and the FP64 arbiter.
+template <bool kApprox, bool kMerge, bool kStats>
+__global__ void __launch_bounds__(kCertThreads, PCR_CERT_MIN_BLOCKS) k_raster_cert(
+    const uint4* __restrict__ pts, uint64_t n, const __grid_constant__ CertParams P,
+    unsigned long long* __restrict__ keys, unsigned long long* __restrict__ stats) {
   __shared__ long long sF[3 * kTableEntries];
+  __shared__ uint4 queue[kCertWarps][kQueue];
   if (!kApprox) load_table(P, sF);
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  uint4* q = queue[warp];
+  uint32_t qn = 0;
+  unsigned c_exact = 0, c_amb = 0, c_fp64 = 0, c_defer = 0;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const uint4 p = ld_stream16(pts + i);
-    const CertFrag f = kApprox ? classify_df(P, p) : classify_cert(P, sF, p);
-    if (f.state == kCulled) continue;
-    uint32_t pix = f.pixel;
-    unsigned long long q = (unsigned long long)f.q;
-    bool accept = false;
-    bool arbiter = f.state == kHard;
-    if (!arbiter) {
-      const unsigned long long qmin = keys[pix] >> 24;
-      accept = in_band(q, qmin, P.v.nq, eps_num, eps_den);
-      if (f.state == kAmbiguous) {
-        const unsigned long long q2 = q + 1 < kQMax ? q + 1 : kQMax;
-        arbiter = accept != in_band(q2, qmin, P.v.nq, eps_num, eps_den);
+  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n; base += stride * kBatch) {
+    uint4 pv[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {  // all loads of the batch first
+      const uint64_t i = base + u * stride + lane;
+      pv[u] = i < n ? ld_stream16(pts + i) : make_uint4(0u, 0u, 0u, 0u);
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const uint64_t i = base + u * stride + lane;
+      const uint4 p = pv[u];
+      bool defer = false, has = false;
+      uint32_t pix = 0;
+      unsigned long long key = 0;
+      if (i < n) {
+        if (kApprox) {
+          const CertFrag f = classify_df(P, p);
+          has = f.state == kExact;
+          pix = f.pixel;
+          key = make_key((unsigned long long)f.q, p.w);
+        } else {
+          const FastFrag f = classify_fast(P, sF, p);
+          pix = f.pixel;
+          key = key_from_fixed(f.a0, f.a1, f.a2, p.w);
+          has = f.state == kExact;
+          defer = f.state == kDefer;
+          if (f.state == kAmbiguous) {
+            // candidates qc - 1, qc (lo_half) or qc, qc + 1: only the smaller one can matter
+            const unsigned long long klo = f.lo_half ? key - (1ull << 24) : key;
+            defer = klo < keys[pix];
+            if (kStats) ++c_amb;
+          }
+          if (kStats) {
+            c_exact += has;
+            c_defer += defer;
+          }
+        }
       }
-    }
-    if (arbiter) {
-      accept = false;
-      if (project_fp64(P.v, __uint_as_float(p.x), __uint_as_float(p.y), __uint_as_float(p.z), &pix, &q))
-        accept = in_band(q, keys[pix] >> 24, P.v.nq, eps_num, eps_den);
-    }
-    if (accept) {
-      atomicAdd(accum + 2 * (uint64_t)pix, hq_rg(p.w));
-      atomicAdd(accum + 2 * (uint64_t)pix + 1, hq_bc(p.w));
+      commit_min<kMerge>(has, pix, key, keys, lane);
+      if (kApprox) continue;
+      defer_points(defer, p, q, qn, lane, [&](const uint4& d) { raster_deferred(P, sF, d, keys, &c_fp64); });
     }
   }
+  if (!kApprox && lane < qn) raster_deferred(P, sF, q[lane], keys, &c_fp64);
+  if (kStats) {
+    atomicAdd(stats + 0, (unsigned long long)c_exact);
+    atomicAdd(stats + 1, (unsigned long long)c_amb);
+    atomicAdd(stats + 2, (unsigned long long)c_fp64);
+    atomicAdd(stats + 3, (unsigned long long)c_defer);
+  }
+}
+
+// Pass-2 decision for a tier-2 result: accept, reject, or (return true) send to the arbiter.
+__device__ __forceinline__ bool hq_decide(const CertParams& P, const CertFrag& f, const unsigned long long* keys,
+                                          uint32_t eps_num, uint32_t eps_den, bool* accept) {
+  *accept = false;
+  if (f.state == kHard) return true;
+  if (f.state != kExact && f.state != kAmbiguous) return false;
+  const unsigned long long qmin = keys[f.pixel] >> 24;
+  const unsigned long long q = (unsigned long long)f.q;
+  *accept = in_band(q, qmin, P.v.nq, eps_num, eps_den);
+  if (f.state == kAmbiguous) {
+    const unsigned long long q2 = q + 1 < kQMax ? q + 1 : kQMax;
+    if (*accept != in_band(q2, qmin, P.v.nq, eps_num, eps_den)) {
+      *accept = false;
+      return true;
+    }
+  }
+  return false;
+}
+
+__device__ __forceinline__ void hq_add(unsigned long long* accum, uint32_t pix, uint32_t rgba) {
+  atomicAdd(accum + 2 * (uint64_t)pix, hq_rg(rgba));
+  atomicAdd(accum + 2 * (uint64_t)pix + 1, hq_bc(rgba));
+}
+
+// Adds the colours of the accepted fragments with one pair of atomics per distinct pixel of the warp
+// (per-channel warp sums: at most 32 * 255, no carry between the packed fields). All lanes must call it.
+template <bool kMerge>
+__device__ __forceinline__ void commit_add(bool add, uint32_t pix, uint32_t rgba, unsigned long long* accum,
+                                           uint32_t lane) {
+  if (!kMerge) {
+    if (add) hq_add(accum, pix, rgba);
+    return;
+  }
+  const unsigned act = __ballot_sync(0xFFFFFFFFu, add);
+  if (add) {
+    const unsigned grp = __match_any_sync(act, pix);
+    const unsigned r = __reduce_add_sync(grp, rgba & 0xFFu);
+    const unsigned g = __reduce_add_sync(grp, (rgba >> 8) & 0xFFu);
+    const unsigned b = __reduce_add_sync(grp, (rgba >> 16) & 0xFFu);
+    if ((grp & ((1u << lane) - 1u)) == 0u) {
+      atomicAdd(accum + 2 * (uint64_t)pix, (unsigned long long)r | ((unsigned long long)g << 32));
+      atomicAdd(accum + 2 * (uint64_t)pix + 1, (unsigned long long)b | ((unsigned long long)__popc(grp) << 32));
+    }
+  }
+}
+
+__device__ __noinline__ void hq_deferred(const CertParams& P, const long long* sF, uint4 p,
+                                         const unsigned long long* keys, unsigned long long* accum, uint32_t eps_num,
+                                         uint32_t eps_den) {
+  const CertFrag f = classify_cert(P, sF, p);
+  bool accept;
+  uint32_t pix = f.pixel;
+  if (hq_decide(P, f, keys, eps_num, eps_den, &accept)) {
+    unsigned long long q;
+    accept = project_fp64(P.v, __uint_as_float(p.x), __uint_as_float(p.y), __uint_as_float(p.z), &pix, &q) &&
+             in_band(q, keys[pix] >> 24, P.v.nq, eps_num, eps_den);
+  }
+  if (accept) hq_add(accum, pix, p.w);
+}
+
+// Pass 2 (Section 2.2) with the certified transform, same two tiers as pass 1.
+template <bool kApprox, bool kMerge>
+__global__ void __launch_bounds__(kCertThreads, PCR_CERT_MIN_BLOCKS) k_hq_cert(
+    const uint4* __restrict__ pts, uint64_t n, const __grid_constant__ CertParams P,
+    const unsigned long long* __restrict__ keys, unsigned long long* __restrict__ accum, uint32_t eps_num,
+    uint32_t eps_den) {
+  __shared__ long long sF[3 * kTableEntries];
+  __shared__ uint4 queue[kCertWarps][kQueue];
+  if (!kApprox) load_table(P, sF);
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  uint4* q = queue[warp];
+  uint32_t qn = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n; base += stride * kBatch) {
+    uint4 pv[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const uint64_t i = base + u * stride + lane;
+      pv[u] = i < n ? ld_stream16(pts + i) : make_uint4(0u, 0u, 0u, 0u);
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const uint64_t i = base + u * stride + lane;
+      const uint4 p = pv[u];
+      bool defer = false, accept = false;
+      uint32_t pix = 0;
+      if (i < n) {
+        if (kApprox) {
+          const CertFrag f = classify_df(P, p);
+          pix = f.pixel;
+          defer = hq_decide(P, f, keys, eps_num, eps_den, &accept);
+        } else {
+          const FastFrag f = classify_fast(P, sF, p);
+          pix = f.pixel;
+          defer = f.state == kDefer;
+          if (f.state == kExact || f.state == kAmbiguous) {
+            const unsigned long long qmin = keys[pix] >> 24;
+            const unsigned long long qc = code_from_fixed(f.a1, f.a2);
+            accept = in_band(f.state == kAmbiguous && f.lo_half ? qc - 1 : qc, qmin, P.v.nq, eps_num, eps_den);
+            if (f.state == kAmbiguous) {
+              const bool other = in_band(f.lo_half ? qc : qc + 1, qmin, P.v.nq, eps_num, eps_den);
+              defer = accept != other;
+              accept = accept && !defer;
+            }
+          }
+        }
+      }
+      commit_add<kMerge>(accept, pix, p.w, accum, lane);
+      if (kApprox) continue;
+      defer_points(defer, p, q, qn, lane,
+                   [&](const uint4& d) { hq_deferred(P, sF, d, keys, accum, eps_num, eps_den); });
+    }
+  }
+  if (!kApprox && lane < qn) hq_deferred(P, sF, q[lane], keys, accum, eps_num, eps_den);
 }
 
 // ---------------------------------------------------------------------------------------------- launch
 
-inline unsigned cert_grid(uint64_t n, int sms) {
-  const uint64_t need = (n + 255) / 256, cap = (uint64_t)sms * 8;
+// Launch tuning (per framebuffer, see pcr_set_tuning): same-pixel merging within a warp, grid size.
+struct Tuning {
+  int merge = 0;
+  int blocks_per_sm = 8;
+};
+
+inline unsigned cert_grid(uint64_t n, int sms, int per_sm) {
+  const uint64_t need = (n + kCertThreads - 1) / kCertThreads, cap = (uint64_t)sms * per_sm;
   return (unsigned)(need < cap ? need : cap);
+}
+
+// Resident blocks per SM of a kernel (cached per process; every device here is the same GB300 part).
+template <typename K>
+inline int resident_blocks(K kernel) {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kCertThreads, 0) != cudaSuccess || b < 1) {
+    cudaGetLastError();
+    b = 1;
+  }
+  return b;
+}
+
+// Grid of a persistent grid-stride launch: never more blocks than can be resident at once.
+inline unsigned persistent_grid(int resident, uint64_t n, int sms, int per_sm) {
+  return cert_grid(n, sms, per_sm < resident ? per_sm : resident);
+}
+
+template <bool kApprox, bool kMerge, bool kStats>
+inline void raster_launch3(const uint4* pts, uint64_t n, const CertParams& P, unsigned long long* keys,
+                           unsigned long long* stats, int sms, int per_sm, cudaStream_t s) {
+  static const int resident = resident_blocks(k_raster_cert<kApprox, kMerge, kStats>);  // one per instantiation
+  const unsigned grid = persistent_grid(resident, n, sms, per_sm);
+  k_raster_cert<kApprox, kMerge, kStats><<<grid, kCertThreads, 0, s>>>(pts, n, P, keys, stats);
+}
+
+template <bool kApprox, bool kMerge>
+inline void raster_launch(const uint4* pts, uint64_t n, const CertParams& P, unsigned long long* keys,
+                          unsigned long long* stats, int sms, int per_sm, cudaStream_t s) {
+  if (stats && !kApprox && !kMerge)
+    raster_launch3<false, false, true>(pts, n, P, keys, stats, sms, per_sm, s);
+  else
+    raster_launch3<kApprox, kMerge, false>(pts, n, P, keys, nullptr, sms, per_sm, s);
 }
 
 inline bool launch_raster_certified(const uint4* pts, uint64_t n, const DevView& v, bool approximate,
                                     unsigned long long* keys, int sms, cudaStream_t s,
-                                    unsigned long long* stats = nullptr) {
+                                    unsigned long long* stats = nullptr, const Tuning& t = Tuning()) {
   static thread_local CertParams P;  // 12.8 KB: kept off the stack
+  const unsigned grid = cert_grid(n, sms, t.blocks_per_sm);
   if (!host::prepare_cert(v, approximate, &P)) {
-    k_raster_fp64<<<cert_grid(n, sms), 256, 0, s>>>(pts, n, v, keys);
+    k_raster_fp64<<<grid, 256, 0, s>>>(pts, n, v, keys);
     return true;
   }
+  const int b = t.blocks_per_sm;
   if (approximate)
-    k_raster_cert<true><<<cert_grid(n, sms), 256, 0, s>>>(pts, n, P, keys, stats);
+    t.merge ? raster_launch<true, true>(pts, n, P, keys, stats, sms, b, s)
+            : raster_launch<true, false>(pts, n, P, keys, stats, sms, b, s);
   else
-    k_raster_cert<false><<<cert_grid(n, sms), 256, 0, s>>>(pts, n, P, keys, stats);
+    t.merge ? raster_launch<false, true>(pts, n, P, keys, stats, sms, b, s)
+            : raster_launch<false, false>(pts, n, P, keys, stats, sms, b, s);
   return true;
+}
+
+template <bool kApprox, bool kMerge>
+inline void hq_launch(const uint4* pts, uint64_t n, const CertParams& P, const unsigned long long* keys,
+                      unsigned long long* accum, uint32_t eps_num, uint32_t eps_den, int sms, int per_sm,
+                      cudaStream_t s) {
+  static const int resident = resident_blocks(k_hq_cert<kApprox, kMerge>);  // one per instantiation
+  const unsigned grid = persistent_grid(resident, n, sms, per_sm);
+  k_hq_cert<kApprox, kMerge><<<grid, kCertThreads, 0, s>>>(pts, n, P, keys, accum, eps_num, eps_den);
 }
 
 inline bool launch_hq_certified(const uint4* pts, uint64_t n, const DevView& v, bool approximate,
                                 const unsigned long long* keys, unsigned long long* accum, uint32_t eps_num,
-                                uint32_t eps_den, int sms, cudaStream_t s) {
+                                uint32_t eps_den, int sms, cudaStream_t s, const Tuning& t = Tuning()) {
   static thread_local CertParams P;
+  const unsigned grid = cert_grid(n, sms, t.blocks_per_sm);
   if (!host::prepare_cert(v, approximate, &P)) {
-    k_hq_fp64<<<cert_grid(n, sms), 256, 0, s>>>(pts, n, v, keys, accum, eps_num, eps_den);
+    k_hq_fp64<<<grid, 256, 0, s>>>(pts, n, v, keys, accum, eps_num, eps_den);
     return true;
   }
+  const int b = t.blocks_per_sm;
   if (approximate)
-    k_hq_cert<true><<<cert_grid(n, sms), 256, 0, s>>>(pts, n, P, keys, accum, eps_num, eps_den);
+    t.merge ? hq_launch<true, true>(pts, n, P, keys, accum, eps_num, eps_den, sms, b, s)
+            : hq_launch<true, false>(pts, n, P, keys, accum, eps_num, eps_den, sms, b, s);
   else
-    k_hq_cert<false><<<cert_grid(n, sms), 256, 0, s>>>(pts, n, P, keys, accum, eps_num, eps_den);
+    t.merge ? hq_launch<false, true>(pts, n, P, keys, accum, eps_num, eps_den, sms, b, s)
+            : hq_launch<false, false>(pts, n, P, keys, accum, eps_num, eps_den, sms, b, s);
   return true;
 }
 

@@ -37,6 +37,10 @@ class pcr_view(ctypes.Structure):
                 ("ranges", (ctypes.c_double * 3) * MAX_DEPTH_RANGES)]
 
 
+class pcr_tuning(ctypes.Structure):
+    _fields_ = [("merge_same_pixel", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+
+
 _P = ctypes.c_void_p
 _lib = None
 
@@ -47,6 +51,9 @@ def _declare(lib):
         "pcr_create_framebuffer": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32, ctypes.POINTER(_P)], S),
         "pcr_destroy_framebuffer": ([_P], S),
         "pcr_framebuffer_info": ([_P, _P, _P, _P], S),
+        "pcr_set_tuning": ([_P, ctypes.POINTER(pcr_tuning)], S),
+        "pcr_get_tuning": ([_P, ctypes.POINTER(pcr_tuning)], S),
+        "pcr_autotune": ([_P, _P, ctypes.c_uint64, ctypes.POINTER(pcr_view), _P, ctypes.POINTER(pcr_tuning)], S),
         "pcr_clear": ([_P, _P], S),
         "pcr_render_atomicmin": ([_P, _P, ctypes.c_uint64, ctypes.POINTER(pcr_view), _P], S),
         "pcr_render_atomicmin_stats": ([_P, _P, ctypes.c_uint64, ctypes.POINTER(pcr_view), _P, _P], S),
@@ -172,6 +179,30 @@ def pcr_framebuffer_info(fb: Framebuffer):
     w, h, f = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_uint32()
     _check(load().pcr_framebuffer_info(fb.handle, ctypes.byref(w), ctypes.byref(h), ctypes.byref(f)))
     return w.value, h.value, f.value
+
+
+def pcr_set_tuning(fb: Framebuffer, merge_same_pixel: int | None = 0, blocks_per_sm: int = 8):
+    """merge_same_pixel=None restores the library defaults."""
+    if merge_same_pixel is None:
+        _check(load().pcr_set_tuning(fb.handle, None))
+    else:
+        t = pcr_tuning(int(merge_same_pixel), int(blocks_per_sm))
+        _check(load().pcr_set_tuning(fb.handle, ctypes.byref(t)))
+
+
+def pcr_get_tuning(fb: Framebuffer):
+    t = pcr_tuning()
+    _check(load().pcr_get_tuning(fb.handle, ctypes.byref(t)))
+    return {"merge_same_pixel": t.merge_same_pixel, "blocks_per_sm": t.blocks_per_sm}
+
+
+def pcr_autotune(fb: Framebuffer, points, view, stream=None):
+    """Times the candidate tunings on one frame of these points and keeps the fastest; returns it."""
+    ptr, n = _points_ptr(points)
+    v = make_view(view)
+    t = pcr_tuning()
+    _check(load().pcr_autotune(fb.handle, ptr, n, ctypes.byref(v), _stream(stream), ctypes.byref(t)))
+    return {"merge_same_pixel": t.merge_same_pixel, "blocks_per_sm": t.blocks_per_sm}
 
 
 def pcr_clear(fb: Framebuffer, stream=None):
