@@ -48,28 +48,28 @@ constexpr int kFixedFracBits = 40;             // t is held in units of 2^-40
 // Per-view constants of the certified evaluation. Passed by value as a __grid_constant__ kernel
 // parameter (about 12.8 KB), so concurrent launches with different views share nothing.
 struct CertParams {
-  DevView v;                          // the FP64 definition (for the arbiter)
-  long long F[3][kTableEntries];      // t-row fixed-point coefficients, index (sign << 8) | exponent
-  float H[3][4], L[3][4];             // double-float splits of the rows clip x, clip y, w
-  float kappa;                        // double-float error bound factor (relative to T)
-  float t_c1, t_c2;                   // FP64-rounding + fixed-point bound of t: t_c1 * T_t + t_c2
-  float Af[3], Bf;                    // float approximations of A_j and B (for T_t)
-  uint32_t B0, B1, B2;                // B * 2^40 as a 96-bit two's-complement integer (low word first)
-  unsigned long long BL;              // tier 1: B * 2^40 = BH * 2^32 + BL, 0 <= BL < 2^32
-  long long BH;
-  int32_t e_max[3];                   // largest biased exponent of x, y, z with a usable table entry
-  long long qn_safe, qn_cull, qf_safe, qf_cull;  // depth-cull thresholds in code space
-  // tier 1: t bound from the float w-row magnitude, D = d_k1 * T_w + d_k2; pixel bound constants
-  float d_k1, d_k2;
+  // hot scalars first: the per-point loops read them as instruction operands; the table comes last
+  float H[3][4], L[3][4];             // float splits of the rows clip x, clip y, w (H: nearest float, L: rest)
   float delta_c;                      // |float(clip) - fma-chain estimate| <= delta_c * T (per row)
-  float ex_a1, ex_a2, ey_a1, ey_a2;   // E = a1 |ndc| + a2 rho + 4.2u |f| + 2^-20 per axis
+  float d_k1, d_k2;                   // tier-1 bound of t: D = d_k1 * T_w + d_k2
   float near_in, far_in;              // w - dw > near_in => w >= near; w + dw < far_in => w < far (FP64 w)
   float near_out, far_out;            // w + dw < near_out => w < near; w - dw > far_out => w >= far
-  float xyz_max;                      // |coordinate| below this: table entries usable, value finite
+  float xyz_max;                      // |x| + |y| + |z| below this: table entries usable, values finite
+  float kappa;                        // double-float error bound factor (relative to T)
+  float t_c1, t_c2;                   // tier-2 bound of t: t_c1 * T_t + t_c2
+  float Af[3], Bf;                    // float approximations of A_j and B (for T_t)
+  float ex_a1, ex_a2, ey_a1, ey_a2;   // tier-1 pixel bound constants (tier 1 folds them per point)
+  unsigned long long BL;              // tier 1: B * 2^40 = BH * 2^32 + BL, 0 <= BL < 2^32
+  long long BH;
+  uint32_t B0, B1, B2;                // B * 2^40 as a 96-bit two's-complement integer (low word first)
+  int32_t e_max[3];                   // largest biased exponent of x, y, z with a usable table entry
+  long long qn_safe, qn_cull, qf_safe, qf_cull;  // depth-cull thresholds in code space
   // approximate (double-float, no arbiter) mode
   float near_h, near_l, far_h, far_l, S_h, S_l;
   int32_t approximate;
   int32_t linear;
+  DevView v;                          // the FP64 definition (for the arbiter)
+  long long F[3][kTableEntries];      // t-row fixed-point coefficients, index (sign << 8) | exponent
 };
 
 // ------------------------------------------------------------------------------------------------ host
@@ -186,8 +186,17 @@ inline bool prepare_cert(const DevView& v, bool approximate, CertParams* P) {
   P->ey_a1 = (float)(3.52 * uf * v.fheight);
   P->ey_a2 = (float)(0.506 * v.fheight);
   // float clip-plane thresholds with (1 +- 4u) margins for the rounding of w -+ dw
-  P->near_in = std::nextafter((float)(v.near_ * (1.0 + 4.0 * uf)), 3.0e38f);
-  P->far_in = std::nextafter((float)(v.far_ * (1.0 - 4.0 * uf)), 0.0f);
+  // near_in also keeps t >= 2.5 and far_in keeps t <= 2^40 - 2^25 for w between them, so the tier-1 code of a
+  // point it certifies as visible needs no sign, zero or cap check (t = S (w - near) or S w)
+  {
+    const double t_lo = 2.5, t_hi = 1099511627776.0 - 33554432.0;
+    const double w_lo = P->linear ? v.near_ + t_lo / S : t_lo / S;
+    const double w_hi = P->linear ? v.near_ + t_hi / S : t_hi / S;
+    const double nin = std::fmax(v.near_ * (1.0 + 4.0 * uf), w_lo * (1.0 + 4.0 * uf));
+    const double fin = std::fmin(v.far_ * (1.0 - 4.0 * uf), w_hi * (1.0 - 4.0 * uf));
+    P->near_in = std::nextafter((float)nin, 3.0e38f);
+    P->far_in = std::nextafter((float)fin, 0.0f);
+  }
   P->near_out = std::nextafter((float)(v.near_ * (1.0 - 4.0 * uf)), 0.0f);
   P->far_out = std::nextafter((float)(v.far_ * (1.0 + 4.0 * uf)), 3.0e38f);
   {
@@ -399,16 +408,19 @@ __device__ __forceinline__ unsigned long long code_from_fixed(uint32_t a1, uint3
 // assembled from predicates at the end.
 __device__ __forceinline__ FastFrag classify_fast(const CertParams& P, const long long* __restrict__ F, uint4 p) {
   const float x = __uint_as_float(p.x), y = __uint_as_float(p.y), z = __uint_as_float(p.z);
-  // finite, and inside the exponent range whose table entries exist (else tier 2 decides)
-  const bool in_range = fabsf(x) < P.xyz_max && fabsf(y) < P.xyz_max && fabsf(z) < P.xyz_max;
+  // finite, and inside the exponent range whose table entries exist (else tier 2 decides): the rounded sum
+  // of the magnitudes is at least each of them, and NaN or infinity fails the comparison
+  const bool in_range = __fadd_rn(__fadd_rn(fabsf(x), fabsf(y)), fabsf(z)) < P.xyz_max;
   // float estimates of w and its term magnitude (fma chains, as the FP64 definition orders them)
   const float w = __fmaf_rn(P.H[2][2], z, __fmaf_rn(P.H[2][1], y, __fmaf_rn(P.H[2][0], x, P.H[2][3])));
   const float Tw = __fmaf_rn(fabsf(P.H[2][2]), fabsf(z),
                              __fmaf_rn(fabsf(P.H[2][1]), fabsf(y), __fmaf_rn(fabsf(P.H[2][0]), fabsf(x), fabsf(P.H[2][3]))));
   const float dw = __fmul_rn(P.delta_c, Tw);
   const float wlo = __fsub_rd(w, dw), whi = __fadd_ru(w, dw);  // directed: wlo <= w - dw, whi >= w + dw
-  const bool depth_out = whi < P.near_out || wlo > P.far_out;
-  const bool depth_in = wlo > P.near_in && whi < P.far_in;
+  // predicates combined with bitwise & and |: every operand is computed anyway, and this keeps the
+  // decision free of short-circuit branches
+  const bool depth_out = (whi < P.near_out) | (wlo > P.far_out);
+  const bool depth_in = (wlo > P.near_in) & (whi < P.far_in);
   // ---- depth code: t * 2^40 = sum m_j F_j + B, accumulated as sum m_j F_lo_j + 2^32 sum m_j F_hi_j
   const long long fx_ = F[p.x >> 23], fy_ = F[kTableEntries + (p.y >> 23)], fz_ = F[2 * kTableEntries + (p.z >> 23)];
   const uint32_t mx = (p.x & 0x7FFFFFu) | 0x800000u, my = (p.y & 0x7FFFFFu) | 0x800000u,
@@ -426,14 +438,14 @@ __device__ __forceinline__ FastFrag classify_fast(const CertParams& P, const lon
   asm("add.cc.u32 %0, %2, %3;\n\taddc.u32 %1, %4, 0;"
       : "=r"(out.a1), "=r"(out.a2)
       : "r"((uint32_t)(L >> 32)), "r"((uint32_t)Hh), "r"((uint32_t)((unsigned long long)Hh >> 32)));
-  const bool code_ok = out.a2 < 0xFFFFu;  // codes in [0, 2^40 - 2^24): no cap, no sign (else tier 2)
   const float frac =
       __fsub_rn(__uint_as_float(0x3F800000u | (__funnelshift_r(out.a0, out.a1, 17) & 0x7FFFFFu)), 1.0f);
   const float D = __fadd_rn(__fmaf_rn(P.d_k1, Tw, P.d_k2), 0x1p-22f);
-  const bool exact = frac > D && frac < __fsub_rn(1.0f, D);
+  // D < frac < 1 - D as |frac - 1/2| < 1/2 - D (frac - 1/2 is exact; the rounding of 1/2 - D is far inside
+  // the 2^-22 slack of D). An undecided code still has two usable candidates while D < 1/4.
+  const bool exact = fabsf(__fsub_rn(frac, 0.5f)) < __fsub_rn(0.5f, D);
   out.lo_half = frac < 0.5f;
-  // an undecided code is usable (two candidates) when the bound is small and the code is not 0 or -1
-  const bool amb_ok = D < 0.25f && !(out.lo_half && out.a2 == 0u && (out.a1 >> 8) == 0u);
+  const bool amb_ok = D < 0.25f;
   // ---- pixel estimate
   const float cx = __fmaf_rn(P.H[0][2], z, __fmaf_rn(P.H[0][1], y, __fmaf_rn(P.H[0][0], x, P.H[0][3])));
   const float Tx = __fmaf_rn(fabsf(P.H[0][2]), fabsf(z),
@@ -459,14 +471,19 @@ __device__ __forceinline__ FastFrag classify_fast(const CertParams& P, const lon
   const float gx = __fadd_rn(__fsub_rn(fx, 0.5f), 12582912.0f), gy = __fadd_rn(__fsub_rn(fy, 0.5f), 12582912.0f);
   const uint32_t kx = (uint32_t)(__float_as_int(gx) - 0x4B400000), ky = (uint32_t)(__float_as_int(gy) - 0x4B400000);
   const float frx = __fsub_rn(fx, __fsub_rn(gx, 12582912.0f)), fry = __fsub_rn(fy, __fsub_rn(gy, 12582912.0f));
-  const bool small_e = Ex < 0.25f && Ey < 0.25f;
-  const bool ax_ok = kx < (uint32_t)P.v.width && frx >= Ex && frx < __fsub_rn(1.0f, Ex) &&
-                     ky < (uint32_t)P.v.height && fry >= Ey && fry < __fsub_rn(1.0f, Ey);
-  const bool ax_out = fx < -Ex || fx >= __fadd_ru(P.v.fwidth, Ex) || fy < -Ey || fy >= __fadd_ru(P.v.fheight, Ey);
-  // ---- state
-  uint32_t st = kDefer;
-  if (in_range && (depth_out || (depth_in && small_e && ax_out))) st = kCulled;
-  else if (in_range && depth_in && small_e && ax_ok && code_ok && (exact || amb_ok)) st = exact ? kExact : kAmbiguous;
+  const bool small_e = __fadd_rn(Ex, Ey) < 0.25f;
+  // E < fr < 1 - E, as |fr - 1/2| < 1/2 - E: the subtraction fr - 1/2 is exact (fr in [-1, 2]), and
+  // rounding 1/2 - E (below 2^-20 from its value) is covered by the 2^-20 slack in E
+  const bool ax_ok = (kx < (uint32_t)P.v.width) & (ky < (uint32_t)P.v.height) &
+                     (fabsf(__fsub_rn(frx, 0.5f)) < __fsub_rn(0.5f, Ex)) & (fabsf(__fsub_rn(fry, 0.5f)) < __fsub_rn(0.5f, Ey));
+  // ---- state (the visible case first; the cull tests only where it fails)
+  uint32_t st;
+  if (in_range & depth_in & small_e & ax_ok & (exact | amb_ok)) {
+    st = exact ? kExact : kAmbiguous;
+  } else {
+    const bool ax_out = (fx < -Ex) | (fx >= __fadd_ru(P.v.fwidth, Ex)) | (fy < -Ey) | (fy >= __fadd_ru(P.v.fheight, Ey));
+    st = in_range & (depth_out | (depth_in & small_e & ax_out)) ? kCulled : kDefer;
+  }
   out.state = st;
   out.pixel = ky * (uint32_t)P.v.width + kx;
   return out;
@@ -530,7 +547,10 @@ __device__ __forceinline__ void load_table(const CertParams& P, long long* sF) {
 #define PCR_CERT_BATCH 2
 #endif
 constexpr int kBatch = PCR_CERT_BATCH;
-constexpr int kCertThreads = 256;
+#ifndef PCR_CERT_THREADS
+#define PCR_CERT_THREADS 256
+#endif
+constexpr int kCertThreads = PCR_CERT_THREADS;
 constexpr int kCertWarps = kCertThreads / 32;
 constexpr int kQueue = 64;  // per-warp deferral queue (points), >= 2 * 32 - 1
 
@@ -611,22 +631,26 @@ __global__ void __launch_bounds__(kCertThreads, PCR_CERT_MIN_BLOCKS) k_raster_ce
   uint4* q = queue[warp];
   uint32_t qn = 0;
   unsigned c_exact = 0, c_amb = 0, c_fp64 = 0, c_defer = 0;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n; base += stride * kBatch) {
+  const uint32_t stride = gridDim.x * blockDim.x;  // below 2^21: 32-bit lane offsets inside an iteration
+  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n;
+       base += (uint64_t)stride * kBatch) {
+    const uint64_t rem64 = n - base;
+    const uint32_t rem = rem64 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)rem64;
+    const uint4* pb = pts + base;
     uint4 pv[kBatch];
 #pragma unroll
     for (int u = 0; u < kBatch; ++u) {  // all loads of the batch first
-      const uint64_t i = base + u * stride + lane;
-      pv[u] = i < n ? ld_stream16(pts + i) : make_uint4(0u, 0u, 0u, 0u);
+      const uint32_t off = u * stride + lane;
+      pv[u] = off < rem ? ld_stream16(pb + off) : make_uint4(0u, 0u, 0u, 0u);
     }
 #pragma unroll
     for (int u = 0; u < kBatch; ++u) {
-      const uint64_t i = base + u * stride + lane;
+      const bool valid = u * stride + lane < rem;
       const uint4 p = pv[u];
       bool defer = false, has = false;
       uint32_t pix = 0;
       unsigned long long key = 0;
-      if (i < n) {
+      if (valid) {
         if (kApprox) {
           const CertFrag f = classify_df(P, p);
           has = f.state == kExact;
@@ -736,21 +760,25 @@ __global__ void __launch_bounds__(kCertThreads, PCR_CERT_MIN_BLOCKS) k_hq_cert(
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   uint4* q = queue[warp];
   uint32_t qn = 0;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n; base += stride * kBatch) {
+  const uint32_t stride = gridDim.x * blockDim.x;  // below 2^21: 32-bit lane offsets inside an iteration
+  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n;
+       base += (uint64_t)stride * kBatch) {
+    const uint64_t rem64 = n - base;
+    const uint32_t rem = rem64 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)rem64;
+    const uint4* pb = pts + base;
     uint4 pv[kBatch];
 #pragma unroll
     for (int u = 0; u < kBatch; ++u) {
-      const uint64_t i = base + u * stride + lane;
-      pv[u] = i < n ? ld_stream16(pts + i) : make_uint4(0u, 0u, 0u, 0u);
+      const uint32_t off = u * stride + lane;
+      pv[u] = off < rem ? ld_stream16(pb + off) : make_uint4(0u, 0u, 0u, 0u);
     }
 #pragma unroll
     for (int u = 0; u < kBatch; ++u) {
-      const uint64_t i = base + u * stride + lane;
+      const bool valid = u * stride + lane < rem;
       const uint4 p = pv[u];
       bool defer = false, accept = false;
       uint32_t pix = 0;
-      if (i < n) {
+      if (valid) {
         if (kApprox) {
           const CertFrag f = classify_df(P, p);
           pix = f.pixel;

@@ -26,12 +26,19 @@ struct DevView {
   int32_t depth_mode, n_ranges;
 };
 
-// 16-byte streaming load that bypasses L1 (each point is read once per pass).
+// 16-byte streaming load (each point is read once per pass): not allocated in L1; with PCR_LOAD_CS the
+// streaming policy (evict first) in both levels, so the stream does not displace the framebuffer in L2.
 __device__ __forceinline__ uint4 ld_stream16(const uint4* p) {
   uint4 v;
+#ifdef PCR_LOAD_CS
+  asm volatile("ld.global.cs.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p));
+#else
   asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
                : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
                : "l"(p));
+#endif
   return v;
 }
 
