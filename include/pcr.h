@@ -194,6 +194,123 @@ const char* pcr_status_string(pcr_status status);
 /* Message of the calling thread's last failed call ("" if none). */
 const char* pcr_last_error_message(void);
 
+
+/* ---------------------------------------------------------------------------------------------------
+ * Batched rendering of a resident cloud: many views per launch (no counterpart in the paper, which
+ * renders one view per frame; the per-point results are those of Sections 2.1 and 2.2).
+ * ------------------------------------------------------------------------------------------------- */
+
+typedef struct pcr_cloud pcr_cloud;
+typedef struct pcr_batch pcr_batch;
+
+#define PCR_CLOUD_CHUNK 1024   /* points per culling chunk */
+#define PCR_MAX_BATCH_VIEWS 256
+
+/* Prepares n caller-owned device points (16-byte aligned, 1 <= n < 2^40) for batched rendering: the
+ * bounding box of every chunk of PCR_CLOUD_CHUNK consecutive points is computed on `stream` into
+ * library-owned device memory (24 B per chunk). The points are not copied: they must stay valid and
+ * unchanged while the cloud is in use. */
+pcr_status pcr_cloud_create(const pcr_point* d_points, uint64_t n, pcr_stream_t stream, pcr_cloud** out);
+
+/* Frees the cloud (synchronises the device). Batches made from it must be destroyed first. NULL is accepted. */
+pcr_status pcr_cloud_destroy(pcr_cloud* cloud);
+
+/* A frame of `count` views of one cloud (1 <= count <= PCR_MAX_BATCH_VIEWS): view i renders into fbs[i]
+ * and resolves into d_outs[i] (caller-owned device memory, width * height u32 of fbs[i]). hq != 0 makes it
+ * a high-quality splatting frame (every fbs[i] created with PCR_FB_HQ; eps_num / eps_den as in
+ * pcr_render_hq_splat). The framebuffers must be distinct, cleared, on the cloud's device, and used by
+ * nothing else while the batch exists. The batch owns its device workspace (per-view constants, visible
+ * chunk lists: 4 B per chunk per view) and a pinned staging buffer for the views. clear_after != 0: every
+ * frame clears the framebuffers after resolving them (ready for the next frame); 0 leaves keys and sums in
+ * place (pcr_framebuffer_keys reads them; clear before the next frame). */
+pcr_status pcr_batch_create(pcr_cloud* cloud, pcr_framebuffer* const* fbs, uint32_t* const* d_outs, int32_t count,
+                            int32_t hq, uint32_t eps_num, uint32_t eps_den, uint32_t background_rgba,
+                            int32_t clear_after, pcr_batch** out);
+
+/* Sets the views of the next frames (count of them). Every view must use LINEAR or METRIC depth within
+ * the single-precision preconditions (every perspective lookAt camera does), else PCR_ERR_INVALID_ARG.
+ * Blocks until the previous frame has copied the earlier views to the device. */
+pcr_status pcr_batch_set_views(pcr_batch* batch, const pcr_view* views);
+
+/* Enqueues one frame on `stream`: copy the views' constants to the device; per view, skip the chunks
+ * whose bounding box is certainly outside the view (behind the near plane, beyond the far plane, or at
+ * |ndc| > 1 + 1e-5, with margins covering every rounding); pass 1 for all views in one persistent
+ * launch; pass 2 (hq) likewise; resolve every framebuffer into its output (and clear it, see
+ * pcr_batch_create). Framebuffer
+ * contents equal those of pcr_render_atomicmin / pcr_render_hq_splat per view, bit for bit. */
+pcr_status pcr_batch_render(pcr_batch* batch, pcr_stream_t stream);
+
+/* Records one frame (as pcr_batch_render) into a CUDA graph owned by the batch; pcr_batch_launch
+ * replays it. Views set later with pcr_batch_set_views are used by later replays. */
+pcr_status pcr_batch_capture(pcr_batch* batch, pcr_stream_t stream);
+
+/* Launches the captured frame graph on `stream`. */
+pcr_status pcr_batch_launch(pcr_batch* batch, pcr_stream_t stream);
+
+/* Visible-chunk counts of the last frame per view (host array of count entries; synchronises the
+ * device). A diagnostic of the culling. */
+pcr_status pcr_batch_visible_chunks(pcr_batch* batch, uint32_t* counts);
+
+/* Frees the batch (synchronises the device). NULL is accepted. */
+pcr_status pcr_batch_destroy(pcr_batch* batch);
+
+/* ---------------------------------------------------------------------------------------------------
+ * Serving: continuous batching of render requests over resident clouds (no counterpart in the paper).
+ * A server thread admits requests while framebuffer memory allows, merges requests that arrive while
+ * others run into shared frames (same cloud, mode, epsilon and background), and runs frames on several
+ * streams so that their work overlaps. Every image equals the single-request result bit for bit.
+ * ------------------------------------------------------------------------------------------------- */
+
+typedef struct pcr_server pcr_server;
+
+typedef struct {
+  int32_t streams;                   /* concurrent frames on the device, 1..16 */
+  int32_t max_batch_views;           /* requests merged into one frame, 1..PCR_MAX_BATCH_VIEWS */
+  uint64_t framebuffer_budget_bytes; /* device memory for the framebuffers of admitted requests (pooled) */
+} pcr_server_config;
+
+typedef struct {
+  int32_t cloud;            /* id from pcr_server_add_cloud */
+  int32_t width, height;    /* 1..16384 */
+  int32_t hq;               /* 0: basic (Section 2.1); 1: high-quality splatting (Section 2.2) */
+  uint32_t eps_num, eps_den;
+  uint32_t background_rgba;
+  int32_t reserved;         /* must be 0 */
+  pcr_view view;            /* LINEAR or METRIC, EXACT transform */
+  uint32_t* d_out;          /* caller-owned device memory, width * height u32, written before completion */
+} pcr_request;
+
+typedef struct {
+  uint64_t id;
+  int32_t status;           /* pcr_status of the request */
+  int32_t batch_views;      /* requests rendered in the same frame */
+  double submit_s, start_s, done_s; /* steady-clock seconds since the server was created */
+} pcr_completion;
+
+/* Creates a server on the current device and starts its scheduling thread. */
+pcr_status pcr_server_create(const pcr_server_config* config, pcr_server** out);
+
+/* Registers a resident cloud (n caller-owned device points, kept unchanged while the server lives) and
+ * returns its id. Synchronous (computes the culling bounds). */
+pcr_status pcr_server_add_cloud(pcr_server* server, const pcr_point* d_points, uint64_t n, int32_t* cloud_id);
+
+/* Queues a request; returns at once with its id. Arguments are checked here (PCR_ERR_INVALID_ARG). A
+ * request larger than the whole framebuffer budget is rejected. The server's streams do not wait on the
+ * caller's streams: the cloud's points must be complete and d_out unused until the request completes. */
+pcr_status pcr_server_submit(pcr_server* server, const pcr_request* request, uint64_t* request_id);
+
+/* Queues count requests at once (all or none: the first invalid one is reported and nothing is queued);
+ * ids[i] receives request i's id. The scheduler sees them together, so requests of one group share frames. */
+pcr_status pcr_server_submit_many(pcr_server* server, const pcr_request* requests, int32_t count, uint64_t* ids);
+
+/* Moves up to max completions into out (oldest first); waits up to wait_ms milliseconds for at least one
+ * when none is ready. *n_out = number written. */
+pcr_status pcr_server_poll(pcr_server* server, pcr_completion* out, int32_t max, int32_t* n_out, int32_t wait_ms);
+
+/* Finishes every submitted request, stops the thread and frees the server (clouds' points stay the
+ * caller's). NULL is accepted. */
+pcr_status pcr_server_destroy(pcr_server* server);
+
 #ifdef __cplusplus
 }
 #endif

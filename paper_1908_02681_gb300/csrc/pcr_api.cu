@@ -7,8 +7,10 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "pcr.h"
+#include "pcr_batch.cuh"
 #include "pcr_certified.cuh"
 #include "pcr_kernels.cuh"
 
@@ -445,3 +447,6 @@ const char* pcr_last_error_message(void) { return g_last_error.c_str(); }
 uint64_t pcr_kernel_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 }  // extern "C"
+
+#include "pcr_batch_api.inc"
+#include "pcr_server.inc"

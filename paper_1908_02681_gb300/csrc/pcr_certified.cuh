@@ -72,6 +72,39 @@ struct CertParams {
   long long F[3][kTableEntries];      // t-row fixed-point coefficients, index (sign << 8) | exponent
 };
 
+// The first-tier constants of one view (a subset of CertParams with the same field names).
+struct HotParams {
+  float H[3][4];
+  float delta_c, d_k1, d_k2, near_in, far_in, near_out, far_out, xyz_max;
+  unsigned long long BL;
+  long long BH;
+  struct {
+    float fwidth, fheight;
+    int32_t width, height;
+  } v;
+};
+
+__host__ __device__ inline HotParams hot_params(const CertParams& P) {
+  HotParams h;
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 4; ++c) h.H[r][c] = P.H[r][c];
+  h.delta_c = P.delta_c;
+  h.d_k1 = P.d_k1;
+  h.d_k2 = P.d_k2;
+  h.near_in = P.near_in;
+  h.far_in = P.far_in;
+  h.near_out = P.near_out;
+  h.far_out = P.far_out;
+  h.xyz_max = P.xyz_max;
+  h.BL = P.BL;
+  h.BH = P.BH;
+  h.v.fwidth = P.v.fwidth;
+  h.v.fheight = P.v.fheight;
+  h.v.width = P.v.width;
+  h.v.height = P.v.height;
+  return h;
+}
+
 // ------------------------------------------------------------------------------------------------ host
 
 namespace host {
@@ -406,7 +439,10 @@ __device__ __forceinline__ unsigned long long code_from_fixed(uint32_t a1, uint3
 // Written without early exits: every quantity is computed for every point (a non-finite coordinate
 // only produces NaN or infinity, which every decision below treats as undecided), and the state is
 // assembled from predicates at the end.
-__device__ __forceinline__ FastFrag classify_fast(const CertParams& P, const long long* __restrict__ F, uint4 p) {
+// PP: CertParams (single-view kernels, read from the kernel parameter block) or HotParams (batched
+// kernels, which hold one view's first-tier constants in registers); both have the fields used here.
+template <typename PP>
+__device__ __forceinline__ FastFrag classify_fast(const PP& P, const long long* __restrict__ F, uint4 p) {
   const float x = __uint_as_float(p.x), y = __uint_as_float(p.y), z = __uint_as_float(p.z);
   // finite, and inside the exponent range whose table entries exist (else tier 2 decides): the rounded sum
   // of the magnitudes is at least each of them, and NaN or infinity fails the comparison

@@ -41,6 +41,23 @@ class pcr_tuning(ctypes.Structure):
     _fields_ = [("merge_same_pixel", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
 
 
+class pcr_server_config(ctypes.Structure):
+    _fields_ = [("streams", ctypes.c_int32), ("max_batch_views", ctypes.c_int32),
+                ("framebuffer_budget_bytes", ctypes.c_uint64)]
+
+
+class pcr_request(ctypes.Structure):
+    _fields_ = [("cloud", ctypes.c_int32), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("hq", ctypes.c_int32), ("eps_num", ctypes.c_uint32), ("eps_den", ctypes.c_uint32),
+                ("background_rgba", ctypes.c_uint32), ("reserved", ctypes.c_int32), ("view", pcr_view),
+                ("d_out", ctypes.c_void_p)]
+
+
+class pcr_completion(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int32), ("batch_views", ctypes.c_int32),
+                ("submit_s", ctypes.c_double), ("start_s", ctypes.c_double), ("done_s", ctypes.c_double)]
+
+
 _P = ctypes.c_void_p
 _lib = None
 
@@ -68,6 +85,22 @@ def _declare(lib):
         "pcr_status_string": ([S], ctypes.c_char_p),
         "pcr_last_error_message": ([], ctypes.c_char_p),
         "pcr_kernel_launch_count": ([], ctypes.c_uint64),
+        "pcr_cloud_create": ([_P, ctypes.c_uint64, _P, ctypes.POINTER(_P)], S),
+        "pcr_cloud_destroy": ([_P], S),
+        "pcr_batch_create": ([_P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint32,
+                              ctypes.c_uint32, ctypes.c_int32, ctypes.POINTER(_P)], S),
+        "pcr_batch_set_views": ([_P, _P], S),
+        "pcr_batch_render": ([_P, _P], S),
+        "pcr_batch_capture": ([_P, _P], S),
+        "pcr_batch_launch": ([_P, _P], S),
+        "pcr_batch_visible_chunks": ([_P, _P], S),
+        "pcr_batch_destroy": ([_P], S),
+        "pcr_server_create": ([ctypes.POINTER(pcr_server_config), ctypes.POINTER(_P)], S),
+        "pcr_server_add_cloud": ([_P, _P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32)], S),
+        "pcr_server_submit": ([_P, ctypes.POINTER(pcr_request), ctypes.POINTER(ctypes.c_uint64)], S),
+        "pcr_server_submit_many": ([_P, _P, ctypes.c_int32, _P], S),
+        "pcr_server_poll": ([_P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32], S),
+        "pcr_server_destroy": ([_P], S),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -286,3 +319,175 @@ def pcr_kernel_launch_count() -> int:
 def keys_to_numpy(t) -> np.ndarray:
     """int64 CUDA tensor of key bit patterns -> host uint64 array."""
     return t.cpu().numpy().view(np.uint64)
+
+
+# ------------------------------------------------------------------------------------- batched rendering
+
+class Cloud:
+    """A resident cloud (pcr_cloud): keeps a reference to the points tensor, which must not change."""
+
+    def __init__(self, handle: int, points):
+        self.handle = ctypes.c_void_p(handle)
+        self.points = points
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            load().pcr_cloud_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pcr_cloud_create(points, stream=None) -> Cloud:
+    ptr, n = _points_ptr(points)
+    out = ctypes.c_void_p()
+    _check(load().pcr_cloud_create(ptr, n, _stream(stream), ctypes.byref(out)))
+    return Cloud(out.value, points)
+
+
+class Batch:
+    """A batch frame (pcr_batch) of len(fbs) views; keeps its cloud, framebuffers and outputs alive."""
+
+    def __init__(self, handle: int, cloud: Cloud, fbs, outs):
+        self.handle = ctypes.c_void_p(handle)
+        self.cloud, self.fbs, self.outs = cloud, list(fbs), list(outs)
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            load().pcr_batch_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pcr_batch_create(cloud: Cloud, fbs, outs, hq: bool = False, eps_num: int = 1, eps_den: int = 100,
+                     background_rgba: int = 0, clear_after: bool = True) -> Batch:
+    n = len(fbs)
+    if len(outs) != n:
+        raise ValueError("one output per framebuffer")
+    fb_arr = (ctypes.c_void_p * n)(*[fb.handle.value for fb in fbs])
+    out_arr = (ctypes.c_void_p * n)(*[_image_ptr(fb, o).value for fb, o in zip(fbs, outs)])
+    h = ctypes.c_void_p()
+    _check(load().pcr_batch_create(cloud.handle, fb_arr, out_arr, n, int(bool(hq)), eps_num, eps_den,
+                                   background_rgba & 0xFFFFFFFF, int(bool(clear_after)), ctypes.byref(h)))
+    return Batch(h.value, cloud, fbs, outs)
+
+
+def pcr_batch_set_views(batch: Batch, views):
+    arr = (pcr_view * len(views))(*[make_view(v) for v in views])
+    _check(load().pcr_batch_set_views(batch.handle, arr))
+
+
+def pcr_batch_render(batch: Batch, stream=None):
+    _check(load().pcr_batch_render(batch.handle, _stream(stream)))
+
+
+def pcr_batch_capture(batch: Batch, stream):
+    _check(load().pcr_batch_capture(batch.handle, _stream(stream)))
+
+
+def pcr_batch_launch(batch: Batch, stream=None):
+    _check(load().pcr_batch_launch(batch.handle, _stream(stream)))
+
+
+def pcr_batch_visible_chunks(batch: Batch) -> list[int]:
+    arr = (ctypes.c_uint32 * len(batch.fbs))()
+    _check(load().pcr_batch_visible_chunks(batch.handle, arr))
+    return list(arr)
+
+
+def pcr_batch_destroy(batch: Batch):
+    batch.close()
+
+
+# ----------------------------------------------------------------------------------------------- serving
+
+class Server:
+    """A render server (pcr_server). Keeps the registered point tensors and the pending outputs alive."""
+
+    def __init__(self, handle: int):
+        self.handle = ctypes.c_void_p(handle)
+        self.points = []
+        self.outputs = {}
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            load().pcr_server_destroy(self.handle)
+        self.handle = None
+        self.outputs.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pcr_server_create(streams: int = 4, max_batch_views: int = 64, framebuffer_budget_bytes: int = 4 << 30) -> Server:
+    cfg = pcr_server_config(streams, max_batch_views, framebuffer_budget_bytes)
+    h = ctypes.c_void_p()
+    _check(load().pcr_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return Server(h.value)
+
+
+def pcr_server_add_cloud(server: Server, points) -> int:
+    ptr, n = _points_ptr(points)
+    cid = ctypes.c_int32()
+    _check(load().pcr_server_add_cloud(server.handle, ptr, n, ctypes.byref(cid)))
+    server.points.append(points)
+    return cid.value
+
+
+def _request(cloud: int, view, out, hq, eps_num, eps_den, background_rgba) -> pcr_request:
+    if out.numel() != view.width * view.height or out.element_size() != 4 or not out.is_contiguous():
+        raise ValueError("out must be a contiguous 4-byte tensor of width*height elements")
+    return pcr_request(cloud, view.width, view.height, int(bool(hq)), eps_num, eps_den, background_rgba & 0xFFFFFFFF, 0,
+                       make_view(view), out.data_ptr())
+
+
+def pcr_server_submit(server: Server, cloud: int, view, out, hq: bool = False, eps_num: int = 1, eps_den: int = 100,
+                      background_rgba: int = 0) -> int:
+    """Queues one render of `view` (its width x height) of cloud `cloud` into the int32 CUDA tensor `out`."""
+    r = _request(cloud, view, out, hq, eps_num, eps_den, background_rgba)
+    rid = ctypes.c_uint64()
+    _check(load().pcr_server_submit(server.handle, ctypes.byref(r), ctypes.byref(rid)))
+    server.outputs[rid.value] = out
+    return rid.value
+
+
+def pcr_server_submit_many(server: Server, requests) -> list[int]:
+    """Queues several requests at once: dicts with cloud, view, out and optional hq, eps_num, eps_den,
+    background_rgba. Returns their ids."""
+    arr = (pcr_request * len(requests))(*[
+        _request(q["cloud"], q["view"], q["out"], q.get("hq", False), q.get("eps_num", 1), q.get("eps_den", 100),
+                 q.get("background_rgba", 0)) for q in requests])
+    ids = (ctypes.c_uint64 * len(requests))()
+    _check(load().pcr_server_submit_many(server.handle, arr, len(requests), ids))
+    for rid, q in zip(ids, requests):
+        server.outputs[rid] = q["out"]
+    return list(ids)
+
+
+def pcr_server_poll(server: Server, max_items: int = 256, wait_ms: int = 0) -> list[dict]:
+    """Completed requests, oldest first: dicts with id, status, batch_views, submit_s, start_s, done_s."""
+    arr = (pcr_completion * max_items)()
+    n = ctypes.c_int32()
+    _check(load().pcr_server_poll(server.handle, arr, max_items, ctypes.byref(n), wait_ms))
+    res = []
+    for c in arr[:n.value]:
+        server.outputs.pop(c.id, None)
+        res.append(dict(id=c.id, status=c.status, batch_views=c.batch_views, submit_s=c.submit_s,
+                        start_s=c.start_s, done_s=c.done_s))
+    return res
+
+
+def pcr_server_destroy(server: Server):
+    server.close()
