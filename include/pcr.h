@@ -255,6 +255,39 @@ pcr_status pcr_batch_visible_chunks(pcr_batch* batch, uint32_t* counts);
 pcr_status pcr_batch_destroy(pcr_batch* batch);
 
 /* ---------------------------------------------------------------------------------------------------
+ * Rendering without device allocation. The paper has no counterpart: its renderer sets up its buffers
+ * once and does not consider callers that cannot allocate.
+ * ------------------------------------------------------------------------------------------------- */
+
+#define PCR_NOALLOC_MAX_VIEWS 8
+#define PCR_NOALLOC_MAX_POINTS 134217728ull /* 2^27 points (131072 chunks of 1024) */
+
+/* One batched frame of count views of n points: the same kernels and the same images as
+ * pcr_cloud_create + pcr_batch_create + pcr_batch_set_views + pcr_batch_render, but the frame's workspace
+ * (chunk bounds, visible lists, per-view constants, counters) is a fixed device array inside libpcr, so
+ * the call allocates nothing: no cudaMalloc, cudaFree or other allocating routine. It is meant for callers
+ * that must not allocate while they render: a render loop in which a cudaMalloc or cudaFree would
+ * synchronise the device and stall other streams; a process held to a fixed device-memory budget or to
+ * its own allocator; code that must still render after an allocation has failed.
+ *
+ * d_points, n: 1..PCR_NOALLOC_MAX_POINTS points (caller-owned device memory, 16-byte aligned).
+ * fbs, d_outs, views, count: 1..PCR_NOALLOC_MAX_VIEWS distinct framebuffers on the current device, their
+ * output images (width * height u32 each) and views, as for pcr_batch_create and pcr_batch_set_views.
+ * hq, eps_num, eps_den, background_rgba, clear_after: as for pcr_batch_create. A larger n or count returns
+ * PCR_ERR_INVALID_ARG, with the limit in pcr_last_error_message(), and enqueues nothing.
+ *
+ * The array takes about 7.4 MB on every device that loads libpcr, until the process exits. The first call
+ * on each device looks up the array's address (cudaGetSymbolAddress) with that device current: make that
+ * first call before any stream capture. All calls on a device share the one array, which keeps what the
+ * last call left in it (each call clears what must start at zero). Calls whose work overlaps on the GPU
+ * (on different streams, or from different host threads without ordering) race on the array and produce
+ * wrong images: put them on one stream or synchronise between them. On the host, calls take a lock. */
+pcr_status pcr_render_views_noalloc(const pcr_point* d_points, uint64_t n, pcr_framebuffer* const* fbs,
+                                    uint32_t* const* d_outs, const pcr_view* views, int32_t count, int32_t hq,
+                                    uint32_t eps_num, uint32_t eps_den, uint32_t background_rgba,
+                                    int32_t clear_after, pcr_stream_t stream);
+
+/* ---------------------------------------------------------------------------------------------------
  * Serving: continuous batching of render requests over resident clouds (no counterpart in the paper).
  * A server thread admits requests while framebuffer memory allows, merges requests that arrive while
  * others run into shared frames (same cloud, mode, epsilon and background), and runs frames on several

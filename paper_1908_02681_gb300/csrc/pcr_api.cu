@@ -450,3 +450,4 @@ uint64_t pcr_kernel_launch_count(void) { return g_launches.load(std::memory_orde
 
 #include "pcr_batch_api.inc"
 #include "pcr_server.inc"
+#include "pcr_noalloc.inc"

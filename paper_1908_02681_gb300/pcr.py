@@ -95,6 +95,8 @@ def _declare(lib):
         "pcr_batch_launch": ([_P, _P], S),
         "pcr_batch_visible_chunks": ([_P, _P], S),
         "pcr_batch_destroy": ([_P], S),
+        "pcr_render_views_noalloc": ([_P, ctypes.c_uint64, _P, _P, _P, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int32, _P], S),
         "pcr_server_create": ([ctypes.POINTER(pcr_server_config), ctypes.POINTER(_P)], S),
         "pcr_server_add_cloud": ([_P, _P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32)], S),
         "pcr_server_submit": ([_P, ctypes.POINTER(pcr_request), ctypes.POINTER(ctypes.c_uint64)], S),
@@ -491,3 +493,24 @@ def pcr_server_poll(server: Server, max_items: int = 256, wait_ms: int = 0) -> l
 
 def pcr_server_destroy(server: Server):
     server.close()
+
+
+# ---------------------------------------------------------------------------------------- no allocation
+
+PCR_NOALLOC_MAX_VIEWS = 8
+PCR_NOALLOC_MAX_POINTS = 1 << 27
+
+
+def pcr_render_views_noalloc(points, fbs, outs, views, hq: bool = False, eps_num: int = 1, eps_den: int = 100,
+                             background_rgba: int = 0, clear_after: bool = True, stream=None):
+    """One batched frame whose workspace is libpcr's fixed device array: allocates no device memory.
+    Calls that overlap on the GPU race on that array (use one stream)."""
+    n = len(fbs)
+    if len(outs) != n or len(views) != n:
+        raise ValueError("one output and one view per framebuffer")
+    ptr, count = _points_ptr(points)
+    fb_arr = (ctypes.c_void_p * n)(*[fb.handle.value for fb in fbs])
+    out_arr = (ctypes.c_void_p * n)(*[_image_ptr(fb, o).value for fb, o in zip(fbs, outs)])
+    view_arr = (pcr_view * n)(*[make_view(v) for v in views])
+    _check(load().pcr_render_views_noalloc(ptr, count, fb_arr, out_arr, view_arr, n, int(bool(hq)), eps_num, eps_den,
+                                           background_rgba & 0xFFFFFFFF, int(bool(clear_after)), _stream(stream)))
