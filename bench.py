@@ -20,7 +20,6 @@ from __future__ import annotations
 
 import argparse
 import ctypes
-import glob
 import hashlib
 import json
 import os
@@ -118,8 +117,10 @@ class ClockSampler:
 
 
 def _csrc_digest() -> str:
+    """Digest of the sources that define the two point-pass kernels (k_raster_cert, k_hq_cert)."""
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1908_02681_gb300", "csrc", "*"))):
+    for name in ("pcr_certified.cuh", "pcr_device.cuh", "pcr_kernels.cuh"):
+        f = os.path.join(ROOT, "paper_1908_02681_gb300", "csrc", name)
         with open(f, "rb") as fh:
             h.update(os.path.basename(f).encode() + fh.read())
     return h.hexdigest()[:16]

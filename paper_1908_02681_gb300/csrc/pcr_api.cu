@@ -152,7 +152,7 @@ pcr_status launch_raster(pcr_framebuffer* fb, const pcr_point* d_points, uint64_
     pcr::k_raster_fp64<<<grid_for(n, 256, fb->device, 8), 256, 0, s>>>(pts, n, dv, fb->keys);
     return after_launch("k_raster_fp64");
   }
-  return pcr::launch_raster_certified(pts, n, dv, transform == PCR_TRANSFORM_DOUBLE_FLOAT, fb->keys,
+  return pcr::launch_raster_certified(pts, n, dv, transform == PCR_TRANSFORM_DOUBLE_FLOAT, fb->keys, fb->status,
                                       sm_count(fb->device), s, stats, fb->tuning)
              ? after_launch("k_raster_certified")
              : fail(PCR_ERR_CUDA, "certified raster launch failed");
@@ -167,7 +167,7 @@ pcr_status launch_hq(pcr_framebuffer* fb, const pcr_point* d_points, uint64_t n,
     return after_launch("k_hq_fp64");
   }
   return pcr::launch_hq_certified(pts, n, dv, transform == PCR_TRANSFORM_DOUBLE_FLOAT, fb->keys, acc, eps_num,
-                                  eps_den, sm_count(fb->device), s, fb->tuning)
+                                  eps_den, fb->status, sm_count(fb->device), s, fb->tuning)
              ? after_launch("k_hq_certified")
              : fail(PCR_ERR_CUDA, "certified HQ launch failed");
 }

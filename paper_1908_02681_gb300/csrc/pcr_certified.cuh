@@ -576,19 +576,102 @@ __device__ __forceinline__ void load_table(const CertParams& P, long long* sF) {
 }
 
 #ifndef PCR_CERT_MIN_BLOCKS
-#define PCR_CERT_MIN_BLOCKS 8
+#define PCR_CERT_MIN_BLOCKS 6
 #endif
-// points loaded per thread before any is processed (memory-level parallelism of the streaming loop)
-#ifndef PCR_CERT_BATCH
-#define PCR_CERT_BATCH 2
-#endif
-constexpr int kBatch = PCR_CERT_BATCH;
 #ifndef PCR_CERT_THREADS
 #define PCR_CERT_THREADS 256
 #endif
 constexpr int kCertThreads = PCR_CERT_THREADS;
 constexpr int kCertWarps = kCertThreads / 32;
 constexpr int kQueue = 64;  // per-warp deferral queue (points), >= 2 * 32 - 1
+
+// ------------------------------------------------------------------------------ point staging (bulk copy)
+//
+// The single-view passes stream the points through shared memory. Each warp owns a two-stage ring of
+// tiles of kTile points (two per lane) and takes the tiles g, g + G, g + 2G, ... of the cloud (g = its
+// warp index in the grid, G = warps in the grid). The bulk-copy engine (cp.async.bulk, completion counted
+// in bytes on one mbarrier per stage) fills one stage while the warp classifies the points of the other,
+// so the warp waits on shared memory instead of on HBM latency. Every wait is bounded; a wait that gives
+// up sets the timeout bit of the framebuffer's status word and the warp stops.
+constexpr int kTile = 64;
+constexpr uint32_t kSpinLimit = 1u << 20;  // try_wait rounds (each may suspend briefly): about a second
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void ring_init(uint64_t* bar) {  // one lane; then __syncwarp
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar + 1)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Copies tile t (if it exists) into dst; one lane. A partial last tile copies only its points (16 B each,
+// so size and both addresses stay multiples of 16 bytes).
+__device__ __forceinline__ void ring_issue(uint4* dst, uint64_t* bar, const uint4* pts, uint64_t n, uint64_t t) {
+  const uint64_t first = t * kTile;
+  if (first >= n) return;
+  const uint64_t left = n - first;
+  const uint32_t bytes = (left < (uint64_t)kTile ? (uint32_t)left : (uint32_t)kTile) * 16u;
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(pts + first), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ bool ring_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+
+// Bounded wait for the completion of the stage's phase with this parity; the same answer in every lane.
+__device__ __forceinline__ bool ring_wait(uint64_t* bar, uint32_t parity) {
+  bool ok = ring_try_wait(bar, parity);
+  if (__any_sync(0xFFFFFFFFu, !ok)) {
+    for (uint32_t spin = 0; !ok && spin < kSpinLimit; ++spin) ok = ring_try_wait(bar, parity);
+    return !__any_sync(0xFFFFFFFFu, !ok);
+  }
+  return true;
+}
+
+// Runs body(p0, valid0, p1, valid1) on every tile of the warp: the lane's two points of the tile; all 32
+// lanes call body together (body may use warp collectives). Returns false when a bounded wait gave up.
+template <typename Body>
+__device__ __forceinline__ bool stream_tiles(const uint4* __restrict__ pts, uint64_t n, uint4 (*ring)[kTile],
+                                             uint64_t* bar, uint32_t lane, Body&& body) {
+  const uint64_t n_tiles = (n + kTile - 1) / kTile;
+  const uint64_t G = (uint64_t)gridDim.x * kCertWarps;
+  const uint64_t g = (uint64_t)blockIdx.x * kCertWarps + (threadIdx.x >> 5);
+  if (lane == 0) {
+    ring_issue(ring[0], &bar[0], pts, n, g);
+    ring_issue(ring[1], &bar[1], pts, n, g + G);
+  }
+  uint32_t s = 0, phases = 0;  // stage of the next tile; bit k = parity of stage k's next phase
+  for (uint64_t t = g; t < n_tiles; t += G) {
+    if (!ring_wait(&bar[s], (phases >> s) & 1u)) {
+      // the other stage's copy (tile t + G) may still be in flight: let it land before the block exits
+      if (t + G < n_tiles) ring_wait(&bar[s ^ 1u], (phases >> (s ^ 1u)) & 1u);
+      return false;
+    }
+    const uint64_t left = n - t * kTile;
+    const uint32_t cnt = left < (uint64_t)kTile ? (uint32_t)left : (uint32_t)kTile;
+    const uint4 p0 = ring[s][lane];
+    const uint4 p1 = ring[s][lane + 32];
+    __syncwarp();
+    if (lane == 0) {  // the stage is free again: refill it with the warp's tile after next
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      ring_issue(ring[s], &bar[s], pts, n, t + 2 * G);
+    }
+    phases ^= 1u << s;
+    s ^= 1u;
+    body(p0, lane < cnt, p1, lane + 32u < cnt);
+  }
+  return true;
+}
 
 // Pass-1 handling of a tier-2 result: returns true when the point still has to go to the FP64 arbiter.
 __device__ __forceinline__ bool raster_commit(const CertFrag& f, uint32_t rgba, unsigned long long* keys) {
@@ -655,66 +738,61 @@ __device__ __forceinline__ void defer_points(bool defer, const uint4& p, uint4* 
 }
 
 // Pass 1 (Section 2.1) with the certified transform. Tier 1 handles nearly every point; the others are
-// queued per warp in shared memory and handled 32 at a time by tier 2 and the FP64 arbiter.
+// queued per warp in shared memory and handled 32 at a time by tier 2 and the FP64 arbiter. The points
+// arrive through the warp's bulk-copy ring (stream_tiles).
 template <bool kApprox, bool kMerge, bool kStats>
 __global__ void __launch_bounds__(kCertThreads, PCR_CERT_MIN_BLOCKS) k_raster_cert(
     const uint4* __restrict__ pts, uint64_t n, const __grid_constant__ CertParams P,
-    unsigned long long* __restrict__ keys, unsigned long long* __restrict__ stats) {
+    unsigned long long* __restrict__ keys, unsigned long long* __restrict__ stats, uint32_t* __restrict__ status) {
   __shared__ long long sF[3 * kTableEntries];
   __shared__ uint4 queue[kCertWarps][kQueue];
-  if (!kApprox) load_table(P, sF);
+  __shared__ __align__(128) uint4 ring[kCertWarps][2][kTile];
+  __shared__ __align__(8) uint64_t bars[kCertWarps][2];
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  if (lane == 0) ring_init(bars[warp]);
+  __syncwarp();
+  if (!kApprox) load_table(P, sF);
   uint4* q = queue[warp];
   uint32_t qn = 0;
   unsigned c_exact = 0, c_amb = 0, c_fp64 = 0, c_defer = 0;
-  const uint32_t stride = gridDim.x * blockDim.x;  // below 2^21: 32-bit lane offsets inside an iteration
-  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n;
-       base += (uint64_t)stride * kBatch) {
-    const uint64_t rem64 = n - base;
-    const uint32_t rem = rem64 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)rem64;
-    const uint4* pb = pts + base;
-    uint4 pv[kBatch];
-#pragma unroll
-    for (int u = 0; u < kBatch; ++u) {  // all loads of the batch first
-      const uint32_t off = u * stride + lane;
-      pv[u] = off < rem ? ld_stream16(pb + off) : make_uint4(0u, 0u, 0u, 0u);
-    }
-#pragma unroll
-    for (int u = 0; u < kBatch; ++u) {
-      const bool valid = u * stride + lane < rem;
-      const uint4 p = pv[u];
-      bool defer = false, has = false;
-      uint32_t pix = 0;
-      unsigned long long key = 0;
-      if (valid) {
-        if (kApprox) {
-          const CertFrag f = classify_df(P, p);
-          has = f.state == kExact;
-          pix = f.pixel;
-          key = make_key((unsigned long long)f.q, p.w);
-        } else {
-          const FastFrag f = classify_fast(P, sF, p);
-          pix = f.pixel;
-          key = key_from_fixed(f.a0, f.a1, f.a2, p.w);
-          has = f.state == kExact;
-          defer = f.state == kDefer;
-          if (f.state == kAmbiguous) {
-            // candidates qc - 1, qc (lo_half) or qc, qc + 1: only the smaller one can matter
-            const unsigned long long klo = f.lo_half ? key - (1ull << 24) : key;
-            defer = klo < keys[pix];
-            if (kStats) ++c_amb;
-          }
-          if (kStats) {
-            c_exact += has;
-            c_defer += defer;
-          }
+  auto point = [&](const uint4& p, bool valid) {
+    bool defer = false, has = false;
+    uint32_t pix = 0;
+    unsigned long long key = 0;
+    if (valid) {
+      if (kApprox) {
+        const CertFrag f = classify_df(P, p);
+        has = f.state == kExact;
+        pix = f.pixel;
+        key = make_key((unsigned long long)f.q, p.w);
+      } else {
+        const FastFrag f = classify_fast(P, sF, p);
+        pix = f.pixel;
+        key = key_from_fixed(f.a0, f.a1, f.a2, p.w);
+        has = f.state == kExact;
+        defer = f.state == kDefer;
+        if (f.state == kAmbiguous) {
+          // candidates qc - 1, qc (lo_half) or qc, qc + 1: only the smaller one can matter
+          const unsigned long long klo = f.lo_half ? key - (1ull << 24) : key;
+          defer = klo < keys[pix];
+          if (kStats) ++c_amb;
+        }
+        if (kStats) {
+          c_exact += has;
+          c_defer += defer;
         }
       }
-      commit_min<kMerge>(has, pix, key, keys, lane);
-      if (kApprox) continue;
-      defer_points(defer, p, q, qn, lane, [&](const uint4& d) { raster_deferred(P, sF, d, keys, &c_fp64); });
     }
-  }
+    commit_min<kMerge>(has, pix, key, keys, lane);
+    if (!kApprox)
+      defer_points(defer, p, q, qn, lane, [&](const uint4& d) { raster_deferred(P, sF, d, keys, &c_fp64); });
+  };
+  const bool done = stream_tiles(pts, n, ring[warp], bars[warp], lane,
+                                 [&](const uint4& p0, bool v0, const uint4& p1, bool v1) {
+                                   point(p0, v0);
+                                   point(p1, v1);
+                                 });
+  if (!done && lane == 0) atomicOr(status, kStatusTimeout);
   if (!kApprox && lane < qn) raster_deferred(P, sF, q[lane], keys, &c_fp64);
   if (kStats) {
     atomicAdd(stats + 0, (unsigned long long)c_exact);
@@ -784,63 +862,81 @@ __device__ __noinline__ void hq_deferred(const CertParams& P, const long long* s
   if (accept) hq_add(accum, pix, p.w);
 }
 
-// Pass 2 (Section 2.2) with the certified transform, same two tiers as pass 1.
+// Pass 2 (Section 2.2) with the certified transform, same two tiers and the same point staging as pass 1.
+// Pass 2 keeps two classified points per lane live across the stored-key reads: 64 registers, 4 blocks
+// per SM (at 40 registers it spills).
+#ifndef PCR_HQ_MIN_BLOCKS
+#define PCR_HQ_MIN_BLOCKS 4
+#endif
 template <bool kApprox, bool kMerge>
-__global__ void __launch_bounds__(kCertThreads, PCR_CERT_MIN_BLOCKS) k_hq_cert(
+__global__ void __launch_bounds__(kCertThreads, PCR_HQ_MIN_BLOCKS) k_hq_cert(
     const uint4* __restrict__ pts, uint64_t n, const __grid_constant__ CertParams P,
     const unsigned long long* __restrict__ keys, unsigned long long* __restrict__ accum, uint32_t eps_num,
-    uint32_t eps_den) {
+    uint32_t eps_den, uint32_t* __restrict__ status) {
   __shared__ long long sF[3 * kTableEntries];
   __shared__ uint4 queue[kCertWarps][kQueue];
-  if (!kApprox) load_table(P, sF);
+  __shared__ __align__(128) uint4 ring[kCertWarps][2][kTile];
+  __shared__ __align__(8) uint64_t bars[kCertWarps][2];
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  if (lane == 0) ring_init(bars[warp]);
+  __syncwarp();
+  if (!kApprox) load_table(P, sF);
   uint4* q = queue[warp];
   uint32_t qn = 0;
-  const uint32_t stride = gridDim.x * blockDim.x;  // below 2^21: 32-bit lane offsets inside an iteration
-  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n;
-       base += (uint64_t)stride * kBatch) {
-    const uint64_t rem64 = n - base;
-    const uint32_t rem = rem64 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)rem64;
-    const uint4* pb = pts + base;
-    uint4 pv[kBatch];
+  // the two points of a tile are classified together so that their stored-key reads overlap
+  const bool done = stream_tiles(pts, n, ring[warp], bars[warp], lane,
+                                 [&](const uint4& p0, bool v0, const uint4& p1, bool v1) {
+    const uint4 pp[2] = {p0, p1};
+    const bool vv[2] = {v0, v1};
+    bool defer[2], accept[2];
+    uint32_t pix[2];
+    if (kApprox) {
 #pragma unroll
-    for (int u = 0; u < kBatch; ++u) {
-      const uint32_t off = u * stride + lane;
-      pv[u] = off < rem ? ld_stream16(pb + off) : make_uint4(0u, 0u, 0u, 0u);
-    }
+      for (int u = 0; u < 2; ++u) {
+        defer[u] = accept[u] = false;
+        pix[u] = 0;
+        if (vv[u]) {
+          const CertFrag f = classify_df(P, pp[u]);
+          pix[u] = f.pixel;
+          defer[u] = hq_decide(P, f, keys, eps_num, eps_den, &accept[u]);
+        }
+      }
+    } else {
+      FastFrag f[2];
+      unsigned long long stored[2];
 #pragma unroll
-    for (int u = 0; u < kBatch; ++u) {
-      const bool valid = u * stride + lane < rem;
-      const uint4 p = pv[u];
-      bool defer = false, accept = false;
-      uint32_t pix = 0;
-      if (valid) {
-        if (kApprox) {
-          const CertFrag f = classify_df(P, p);
-          pix = f.pixel;
-          defer = hq_decide(P, f, keys, eps_num, eps_den, &accept);
-        } else {
-          const FastFrag f = classify_fast(P, sF, p);
-          pix = f.pixel;
-          defer = f.state == kDefer;
-          if (f.state == kExact || f.state == kAmbiguous) {
-            const unsigned long long qmin = keys[pix] >> 24;
-            const unsigned long long qc = code_from_fixed(f.a1, f.a2);
-            accept = in_band(f.state == kAmbiguous && f.lo_half ? qc - 1 : qc, qmin, P.v.nq, eps_num, eps_den);
-            if (f.state == kAmbiguous) {
-              const bool other = in_band(f.lo_half ? qc : qc + 1, qmin, P.v.nq, eps_num, eps_den);
-              defer = accept != other;
-              accept = accept && !defer;
-            }
+      for (int u = 0; u < 2; ++u) {
+        f[u] = classify_fast(P, sF, pp[u]);
+        pix[u] = f[u].pixel;
+        const bool coded = vv[u] & ((f[u].state == kExact) | (f[u].state == kAmbiguous));
+        stored[u] = coded ? keys[pix[u]] : 0ull;
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        defer[u] = vv[u] & (f[u].state == kDefer);
+        accept[u] = false;
+        if (vv[u] & ((f[u].state == kExact) | (f[u].state == kAmbiguous))) {
+          const unsigned long long qmin = stored[u] >> 24;
+          const unsigned long long qc = code_from_fixed(f[u].a1, f[u].a2);
+          const bool amb = f[u].state == kAmbiguous;
+          accept[u] = in_band(amb && f[u].lo_half ? qc - 1 : qc, qmin, P.v.nq, eps_num, eps_den);
+          if (amb) {
+            const bool other = in_band(f[u].lo_half ? qc : qc + 1, qmin, P.v.nq, eps_num, eps_den);
+            defer[u] = accept[u] != other;
+            accept[u] = accept[u] && !defer[u];
           }
         }
       }
-      commit_add<kMerge>(accept, pix, p.w, accum, lane);
-      if (kApprox) continue;
-      defer_points(defer, p, q, qn, lane,
-                   [&](const uint4& d) { hq_deferred(P, sF, d, keys, accum, eps_num, eps_den); });
     }
-  }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      commit_add<kMerge>(accept[u], pix[u], pp[u].w, accum, lane);
+      if (!kApprox)
+        defer_points(defer[u], pp[u], q, qn, lane,
+                     [&](const uint4& d) { hq_deferred(P, sF, d, keys, accum, eps_num, eps_den); });
+    }
+  });
+  if (!done && lane == 0) atomicOr(status, kStatusTimeout);
   if (!kApprox && lane < qn) hq_deferred(P, sF, q[lane], keys, accum, eps_num, eps_den);
 }
 
@@ -875,23 +971,24 @@ inline unsigned persistent_grid(int resident, uint64_t n, int sms, int per_sm) {
 
 template <bool kApprox, bool kMerge, bool kStats>
 inline void raster_launch3(const uint4* pts, uint64_t n, const CertParams& P, unsigned long long* keys,
-                           unsigned long long* stats, int sms, int per_sm, cudaStream_t s) {
+                           unsigned long long* stats, uint32_t* status, int sms, int per_sm, cudaStream_t s) {
   static const int resident = resident_blocks(k_raster_cert<kApprox, kMerge, kStats>);  // one per instantiation
   const unsigned grid = persistent_grid(resident, n, sms, per_sm);
-  k_raster_cert<kApprox, kMerge, kStats><<<grid, kCertThreads, 0, s>>>(pts, n, P, keys, stats);
+  k_raster_cert<kApprox, kMerge, kStats><<<grid, kCertThreads, 0, s>>>(pts, n, P, keys, stats, status);
 }
 
 template <bool kApprox, bool kMerge>
 inline void raster_launch(const uint4* pts, uint64_t n, const CertParams& P, unsigned long long* keys,
-                          unsigned long long* stats, int sms, int per_sm, cudaStream_t s) {
+                          unsigned long long* stats, uint32_t* status, int sms, int per_sm, cudaStream_t s) {
   if (stats && !kApprox && !kMerge)
-    raster_launch3<false, false, true>(pts, n, P, keys, stats, sms, per_sm, s);
+    raster_launch3<false, false, true>(pts, n, P, keys, stats, status, sms, per_sm, s);
   else
-    raster_launch3<kApprox, kMerge, false>(pts, n, P, keys, nullptr, sms, per_sm, s);
+    raster_launch3<kApprox, kMerge, false>(pts, n, P, keys, nullptr, status, sms, per_sm, s);
 }
 
+// Pass 1 for a view with n >= 1 points. status: the framebuffer's status word (timeout bit).
 inline bool launch_raster_certified(const uint4* pts, uint64_t n, const DevView& v, bool approximate,
-                                    unsigned long long* keys, int sms, cudaStream_t s,
+                                    unsigned long long* keys, uint32_t* status, int sms, cudaStream_t s,
                                     unsigned long long* stats = nullptr, const Tuning& t = Tuning()) {
   static thread_local CertParams P;  // 12.8 KB: kept off the stack
   const unsigned grid = cert_grid(n, sms, t.blocks_per_sm);
@@ -901,26 +998,28 @@ inline bool launch_raster_certified(const uint4* pts, uint64_t n, const DevView&
   }
   const int b = t.blocks_per_sm;
   if (approximate)
-    t.merge ? raster_launch<true, true>(pts, n, P, keys, stats, sms, b, s)
-            : raster_launch<true, false>(pts, n, P, keys, stats, sms, b, s);
+    t.merge ? raster_launch<true, true>(pts, n, P, keys, stats, status, sms, b, s)
+            : raster_launch<true, false>(pts, n, P, keys, stats, status, sms, b, s);
   else
-    t.merge ? raster_launch<false, true>(pts, n, P, keys, stats, sms, b, s)
-            : raster_launch<false, false>(pts, n, P, keys, stats, sms, b, s);
+    t.merge ? raster_launch<false, true>(pts, n, P, keys, stats, status, sms, b, s)
+            : raster_launch<false, false>(pts, n, P, keys, stats, status, sms, b, s);
   return true;
 }
 
 template <bool kApprox, bool kMerge>
 inline void hq_launch(const uint4* pts, uint64_t n, const CertParams& P, const unsigned long long* keys,
-                      unsigned long long* accum, uint32_t eps_num, uint32_t eps_den, int sms, int per_sm,
-                      cudaStream_t s) {
+                      unsigned long long* accum, uint32_t eps_num, uint32_t eps_den, uint32_t* status, int sms,
+                      int per_sm, cudaStream_t s) {
   static const int resident = resident_blocks(k_hq_cert<kApprox, kMerge>);  // one per instantiation
   const unsigned grid = persistent_grid(resident, n, sms, per_sm);
-  k_hq_cert<kApprox, kMerge><<<grid, kCertThreads, 0, s>>>(pts, n, P, keys, accum, eps_num, eps_den);
+  k_hq_cert<kApprox, kMerge><<<grid, kCertThreads, 0, s>>>(pts, n, P, keys, accum, eps_num, eps_den, status);
 }
 
+// Pass 2 for a view with n >= 1 points. status: the framebuffer's status word (timeout bit).
 inline bool launch_hq_certified(const uint4* pts, uint64_t n, const DevView& v, bool approximate,
                                 const unsigned long long* keys, unsigned long long* accum, uint32_t eps_num,
-                                uint32_t eps_den, int sms, cudaStream_t s, const Tuning& t = Tuning()) {
+                                uint32_t eps_den, uint32_t* status, int sms, cudaStream_t s,
+                                const Tuning& t = Tuning()) {
   static thread_local CertParams P;
   const unsigned grid = cert_grid(n, sms, t.blocks_per_sm);
   if (!host::prepare_cert(v, approximate, &P)) {
@@ -929,11 +1028,11 @@ inline bool launch_hq_certified(const uint4* pts, uint64_t n, const DevView& v, 
   }
   const int b = t.blocks_per_sm;
   if (approximate)
-    t.merge ? hq_launch<true, true>(pts, n, P, keys, accum, eps_num, eps_den, sms, b, s)
-            : hq_launch<true, false>(pts, n, P, keys, accum, eps_num, eps_den, sms, b, s);
+    t.merge ? hq_launch<true, true>(pts, n, P, keys, accum, eps_num, eps_den, status, sms, b, s)
+            : hq_launch<true, false>(pts, n, P, keys, accum, eps_num, eps_den, status, sms, b, s);
   else
-    t.merge ? hq_launch<false, true>(pts, n, P, keys, accum, eps_num, eps_den, sms, b, s)
-            : hq_launch<false, false>(pts, n, P, keys, accum, eps_num, eps_den, sms, b, s);
+    t.merge ? hq_launch<false, true>(pts, n, P, keys, accum, eps_num, eps_den, status, sms, b, s)
+            : hq_launch<false, false>(pts, n, P, keys, accum, eps_num, eps_den, status, sms, b, s);
   return true;
 }
 
