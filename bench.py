@@ -140,6 +140,31 @@ def _traffic(kernel: str, workload: str, n: int):
         return None
 
 
+def host_cpu() -> dict:
+    """The host the oracle runs on: CPU model and logical core count."""
+    model = None
+    try:  # lscpu names Arm cores too (their /proc/cpuinfo has no model line)
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in ([] if model else open("/proc/cpuinfo")):
+            key = line.split(":")[0].strip().lower()
+            if key in ("model name", "cpu model", "hardware"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    if model is None:
+        import platform
+        model = platform.processor() or platform.machine()
+    return {"model": model, "nproc": os.cpu_count()}
+
+
 def max_over_ranks(ms: float, dist=None, device=None) -> float:
     """Time of the slowest rank (replicas: the job ends with its last rank); ms itself without dist."""
     if dist is None:
@@ -187,7 +212,8 @@ def run_reference(args, wl):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl["desc"], "points_per_step": sample_n},
-        "cpu_baseline": {"value": value, "unit": "Gpts/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "Gpts/s", "cores": 1, "kind": "oracle", "sample": sample,
+                         "host": host_cpu()},
         "e2e": {"value": value, "unit": "Gpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
 
 
@@ -364,6 +390,7 @@ def run_ours(args, wl):
         sample = host[:sample_n].numpy().view(np.uint32)
         t = cpu_oracle_frame(sample, view)
         result["cpu_baseline"] = {"value": sample_n / t / 1e9, "unit": "Gpts/s", "cores": 1, "kind": "oracle",
+                                  "host": host_cpu(),
                                   "sample": f"first {sample_n} points of the workload, one full frame "
                                             f"(both passes and resolves), {t:.1f} s"}
     print(json.dumps(result), flush=True)
