@@ -179,6 +179,14 @@ pcr_status pcr_resolve_basic(pcr_framebuffer* fb, uint32_t* d_rgba_out, uint32_t
  * pcr_destroy_framebuffer. Either output pointer may be NULL. */
 pcr_status pcr_framebuffer_keys(const pcr_framebuffer* fb, const uint64_t** d_keys, const uint64_t** d_accum);
 
+/* Check of the timeout path (no counterpart in the paper). The point passes wait on shared-memory barriers
+ * for their bulk copies, and every such wait gives up after a bounded number of rounds, sets fb's timeout
+ * bit and ends the pass, so that a copy that never lands shows up as PCR_ERR_TIMEOUT from
+ * pcr_get_device_status instead of a hung kernel. This call runs that wait routine in one warp on a
+ * barrier that nothing will complete (no copy is issued), so it gives up after `rounds` rounds (1..2^18;
+ * 0 = the passes' own limit of 2^18 rounds, about 1 s on GB300) and sets the bit. Asynchronous on `stream`. */
+pcr_status pcr_check_bounded_wait(pcr_framebuffer* fb, uint32_t rounds, pcr_stream_t stream);
+
 /* Synchronises `stream`, then returns and resets the device-side status of fb: PCR_ERR_OVERFLOW if an
  * HQ resolve found a pixel with more than 2^24 fragments, PCR_ERR_TIMEOUT if a bounded wait gave up,
  * else PCR_OK. */

@@ -430,6 +430,13 @@ pcr_status pcr_get_device_status(pcr_framebuffer* fb, pcr_stream_t stream) {
   return PCR_OK;
 }
 
+pcr_status pcr_check_bounded_wait(pcr_framebuffer* fb, uint32_t rounds, pcr_stream_t stream) {
+  if (pcr_status st = check_fb(fb)) return st;
+  if (rounds > pcr::kSpinLimit) return fail(PCR_ERR_INVALID_ARG, "rounds must be at most %u", pcr::kSpinLimit);
+  pcr::k_wait_check<<<1, 32, 0, (cudaStream_t)stream>>>(fb->status, rounds ? rounds : pcr::kSpinLimit);
+  return after_launch("k_wait_check");
+}
+
 const char* pcr_status_string(pcr_status status) {
   switch (status) {
     case PCR_OK: return "PCR_OK";

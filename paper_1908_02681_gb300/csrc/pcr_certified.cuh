@@ -594,7 +594,7 @@ constexpr int kQueue = 64;  // per-warp deferral queue (points), >= 2 * 32 - 1
 // so the warp waits on shared memory instead of on HBM latency. Every wait is bounded; a wait that gives
 // up sets the timeout bit of the framebuffer's status word and the warp stops.
 constexpr int kTile = 64;
-constexpr uint32_t kSpinLimit = 1u << 20;  // try_wait rounds (each may suspend briefly): about a second
+constexpr uint32_t kSpinLimit = 1u << 18;  // try_wait rounds; a round that fails suspends ~3.9 us: about 1 s
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -629,13 +629,22 @@ __device__ __forceinline__ bool ring_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Bounded wait for the completion of the stage's phase with this parity; the same answer in every lane.
-__device__ __forceinline__ bool ring_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool ring_wait(uint64_t* bar, uint32_t parity, uint32_t limit = kSpinLimit) {
   bool ok = ring_try_wait(bar, parity);
   if (__any_sync(0xFFFFFFFFu, !ok)) {
-    for (uint32_t spin = 0; !ok && spin < kSpinLimit; ++spin) ok = ring_try_wait(bar, parity);
+    for (uint32_t spin = 0; !ok && spin < limit; ++spin) ok = ring_try_wait(bar, parity);
     return !__any_sync(0xFFFFFFFFu, !ok);
   }
   return true;
+}
+
+// Check of the timeout path: one warp waits, with the passes' ring_wait, on a stage barrier that no copy
+// will ever complete (nothing is in flight), gives up after `limit` rounds and sets the timeout bit.
+__global__ void k_wait_check(uint32_t* __restrict__ status, uint32_t limit) {
+  __shared__ __align__(8) uint64_t bar[2];
+  if (threadIdx.x == 0) ring_init(bar);
+  __syncwarp();
+  if (!ring_wait(&bar[0], 0u, limit) && threadIdx.x == 0) atomicOr(status, kStatusTimeout);
 }
 
 // Runs body(p0, valid0, p1, valid1) on every tile of the warp: the lane's two points of the tile; all 32

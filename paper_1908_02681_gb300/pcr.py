@@ -82,6 +82,7 @@ def _declare(lib):
         "pcr_resolve_basic": ([_P, _P, ctypes.c_uint32, ctypes.c_int32, _P], S),
         "pcr_framebuffer_keys": ([_P, ctypes.POINTER(_P), ctypes.POINTER(_P)], S),
         "pcr_get_device_status": ([_P, _P], S),
+        "pcr_check_bounded_wait": ([_P, ctypes.c_uint32, _P], S),
         "pcr_status_string": ([S], ctypes.c_char_p),
         "pcr_last_error_message": ([], ctypes.c_char_p),
         "pcr_kernel_launch_count": ([], ctypes.c_uint64),
@@ -304,6 +305,11 @@ def pcr_framebuffer_keys(fb: Framebuffer):
 def pcr_get_device_status(fb: Framebuffer, stream=None) -> int:
     """Synchronises the stream and returns (and resets) the framebuffer's device status code."""
     return int(load().pcr_get_device_status(fb.handle, _stream(stream)))
+
+
+def pcr_check_bounded_wait(fb: Framebuffer, rounds: int = 1024, stream=None):
+    """Runs the passes' bounded barrier wait on a barrier nothing completes: sets fb's timeout bit."""
+    _check(load().pcr_check_bounded_wait(fb.handle, rounds, _stream(stream)))
 
 
 def pcr_status_string(status: int) -> str:
