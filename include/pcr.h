@@ -179,6 +179,22 @@ pcr_status pcr_resolve_basic(pcr_framebuffer* fb, uint32_t* d_rgba_out, uint32_t
  * pcr_destroy_framebuffer. Either output pointer may be NULL. */
 pcr_status pcr_framebuffer_keys(const pcr_framebuffer* fb, const uint64_t** d_keys, const uint64_t** d_accum);
 
+/* One complete frame from host memory (Sections 2.1 and 2.2 end to end). It:
+ *   - copies the n points from h_points (host memory; pinned for the copies to overlap) into d_points
+ *     (caller-owned device buffer of n points, 16-byte aligned) in up to 8 chunks, and runs pass 1 on each
+ *     chunk as soon as it has landed;
+ *   - then pass 2 (HQ framebuffers), the basic resolve into d_images[0, W*H) and the HQ resolve into
+ *     d_images[W*H, 2*W*H), clearing fb;
+ *   - copies the images to h_basic and h_hq (host, W*H u32 each; h_hq is unused without PCR_FB_HQ).
+ * d_images: caller-owned device scratch of 2*W*H u32. The frame must start from a cleared fb; it leaves fb
+ * cleared. Everything is enqueued on `stream`, plus fb's internal copy stream, which is ordered with
+ * `stream` by events and created, with its events, by the first call on fb. The call returns at once:
+ * synchronise `stream` before reading the host images or reusing h_points or d_points. Requirements as for
+ * pcr_render_hq_splat (HQ) or pcr_render_atomicmin. */
+pcr_status pcr_render_frame_host(pcr_framebuffer* fb, const pcr_point* h_points, uint64_t n, const pcr_view* view,
+                                 uint32_t eps_num, uint32_t eps_den, uint32_t background_rgba, pcr_point* d_points,
+                                 uint32_t* d_images, uint32_t* h_basic, uint32_t* h_hq, pcr_stream_t stream);
+
 /* Check of the timeout path (no counterpart in the paper). The point passes wait on shared-memory barriers
  * for their bulk copies, and every such wait gives up after a bounded number of rounds, sets fb's timeout
  * bit and ends the pass, so that a copy that never lands shows up as PCR_ERR_TIMEOUT from

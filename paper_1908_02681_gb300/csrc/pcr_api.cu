@@ -22,6 +22,9 @@ struct pcr_framebuffer {
   ulonglong2* accum;         // width * height (HQ only)
   uint32_t* status;          // device status word
   pcr::Tuning tuning;        // launch tuning of the point passes
+  // frames from host memory (pcr_render_frame_host): copy stream and events, created by its first call
+  cudaStream_t copy_stream;
+  cudaEvent_t copy_events[9];  // [0]: start of the frame on the caller's stream; [1..8]: chunk k landed
 };
 
 namespace {
@@ -229,6 +232,10 @@ pcr_status pcr_destroy_framebuffer(pcr_framebuffer* fb) {
   cudaFree(fb->keys);
   cudaFree(fb->accum);
   cudaFree(fb->status);
+  if (fb->copy_stream) {
+    cudaStreamDestroy(fb->copy_stream);
+    for (cudaEvent_t e : fb->copy_events) cudaEventDestroy(e);
+  }
   cudaSetDevice(prev);
   delete fb;
   return PCR_OK;
@@ -427,6 +434,63 @@ pcr_status pcr_get_device_status(pcr_framebuffer* fb, pcr_stream_t stream) {
   if (word & pcr::kStatusOverflow)
     return fail(PCR_ERR_OVERFLOW, "an HQ pixel received more than 2^24 contributing fragments");
   if (word & pcr::kStatusTimeout) return fail(PCR_ERR_TIMEOUT, "a bounded device-side wait gave up");
+  return PCR_OK;
+}
+
+pcr_status pcr_render_frame_host(pcr_framebuffer* fb, const pcr_point* h_points, uint64_t n, const pcr_view* view,
+                                 uint32_t eps_num, uint32_t eps_den, uint32_t background_rgba, pcr_point* d_points,
+                                 uint32_t* d_images, uint32_t* h_basic, uint32_t* h_hq, pcr_stream_t stream) {
+  const bool hq = fb && (fb->flags & PCR_FB_HQ);
+  pcr::DevView dv;
+  if (hq) {
+    if (pcr_status st = check_hq(fb, d_points, n, view, eps_num, eps_den, &dv)) return st;
+  } else {
+    if (pcr_status st = check_fb(fb)) return st;
+    if (pcr_status st = check_points(d_points, n)) return st;
+    if (pcr_status st = make_dev_view(view, fb->width, fb->height, &dv)) return st;
+  }
+  if (n > 0 && !h_points) return fail(PCR_ERR_INVALID_ARG, "h_points is NULL");
+  if (!d_images || !h_basic || (hq && !h_hq)) return fail(PCR_ERR_INVALID_ARG, "d_images and the host images are required");
+  const cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (!fb->copy_stream) {  // first call on this framebuffer
+    e = cudaStreamCreateWithFlags(&fb->copy_stream, cudaStreamNonBlocking);
+    for (int k = 0; k < 9 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&fb->copy_events[k], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      if (fb->copy_stream) cudaStreamDestroy(fb->copy_stream);
+      for (cudaEvent_t& ev : fb->copy_events) {
+        if (ev) cudaEventDestroy(ev);
+        ev = nullptr;
+      }
+      fb->copy_stream = nullptr;
+      return cuda_fail(e, "copy stream");
+    }
+  }
+  // the copies into d_points wait for earlier work on the caller's stream (which may still read them)
+  e = cudaEventRecord(fb->copy_events[0], s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(fb->copy_stream, fb->copy_events[0], 0);
+  if (e != cudaSuccess) return cuda_fail(e, "frame start");
+  // up to 8 chunks: pass 1 of chunk k runs while chunk k + 1 is still being copied
+  const uint64_t chunks = n < (8ull << 20) ? 1 : 8;
+  for (uint64_t k = 0; k < chunks && n > 0; ++k) {
+    const uint64_t lo = n * k / chunks, hi = n * (k + 1) / chunks;
+    if (hi == lo) continue;
+    e = cudaMemcpyAsync(d_points + lo, h_points + lo, (hi - lo) * sizeof(pcr_point), cudaMemcpyHostToDevice,
+                        fb->copy_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(fb->copy_events[1 + k], fb->copy_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, fb->copy_events[1 + k], 0);
+    if (e != cudaSuccess) return cuda_fail(e, "point upload");
+    if (pcr_status st = launch_raster(fb, d_points + lo, hi - lo, dv, view->transform, s)) return st;
+  }
+  if (hq && n > 0)
+    if (pcr_status st = launch_hq(fb, d_points, n, dv, view->transform, eps_num, eps_den, s)) return st;
+  const uint64_t npx = (uint64_t)fb->width * fb->height;
+  if (pcr_status st = pcr_resolve_basic(fb, d_images, background_rgba, hq ? 0 : 1, stream)) return st;
+  if (hq)
+    if (pcr_status st = pcr_resolve(fb, d_images + npx, background_rgba, 1, stream)) return st;
+  e = cudaMemcpyAsync(h_basic, d_images, npx * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && hq) e = cudaMemcpyAsync(h_hq, d_images + npx, npx * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(e, "image download");
   return PCR_OK;
 }
 

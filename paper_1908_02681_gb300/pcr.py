@@ -83,6 +83,8 @@ def _declare(lib):
         "pcr_framebuffer_keys": ([_P, ctypes.POINTER(_P), ctypes.POINTER(_P)], S),
         "pcr_get_device_status": ([_P, _P], S),
         "pcr_check_bounded_wait": ([_P, ctypes.c_uint32, _P], S),
+        "pcr_render_frame_host": ([_P, _P, ctypes.c_uint64, ctypes.POINTER(pcr_view), ctypes.c_uint32, ctypes.c_uint32,
+                                   ctypes.c_uint32, _P, _P, _P, _P, _P], S),
         "pcr_status_string": ([S], ctypes.c_char_p),
         "pcr_last_error_message": ([], ctypes.c_char_p),
         "pcr_kernel_launch_count": ([], ctypes.c_uint64),
@@ -305,6 +307,25 @@ def pcr_framebuffer_keys(fb: Framebuffer):
 def pcr_get_device_status(fb: Framebuffer, stream=None) -> int:
     """Synchronises the stream and returns (and resets) the framebuffer's device status code."""
     return int(load().pcr_get_device_status(fb.handle, _stream(stream)))
+
+
+def pcr_render_frame_host(fb: Framebuffer, h_points, view, d_points, d_images, h_basic, h_hq=None,
+                          eps_num: int = 1, eps_den: int = 100, background_rgba: int = 0, stream=None):
+    """One frame from host memory: h_points (CPU int32 (n, 4) tensor, pinned for overlap) is copied into
+    d_points (CUDA tensor of the same shape), rendered, resolved, and the images land in h_basic / h_hq (CPU
+    int32 tensors of W*H). d_images: CUDA int32 scratch of 2*W*H. Asynchronous on `stream`."""
+    n = h_points.shape[0]
+    if tuple(d_points.shape) != tuple(h_points.shape) or not d_points.is_cuda or h_points.is_cuda:
+        raise ValueError("h_points must be a host tensor and d_points a CUDA tensor of the same shape")
+    npx = fb.width * fb.height
+    if d_images.numel() < 2 * npx or h_basic.numel() < npx or (h_hq is not None and h_hq.numel() < npx):
+        raise ValueError("image buffers too small")
+    v = make_view(view)
+    _check(load().pcr_render_frame_host(fb.handle, ctypes.c_void_p(h_points.data_ptr()), n, ctypes.byref(v), eps_num,
+                                        eps_den, background_rgba & 0xFFFFFFFF, ctypes.c_void_p(d_points.data_ptr()),
+                                        ctypes.c_void_p(d_images.data_ptr()), ctypes.c_void_p(h_basic.data_ptr()),
+                                        ctypes.c_void_p(h_hq.data_ptr()) if h_hq is not None else None,
+                                        _stream(stream)))
 
 
 def pcr_check_bounded_wait(fb: Framebuffer, rounds: int = 1024, stream=None):
