@@ -192,13 +192,26 @@ __global__ void __launch_bounds__(kCertThreads, PCR_BATCH_MIN_BLOCKS) k_batch_pa
     const uint32_t last = min(first + (uint32_t)kSlice, counts[v]);
     const uint32_t* list = lists + (uint64_t)v * n_chunks;
     uint32_t qn = 0;
-    for (uint32_t ci = first; ci < last; ++ci) {
-      const uint64_t base = (uint64_t)list[ci] * kChunk;
+    // the item's points as one sequence of steps (kChunk / kCertThreads per chunk); the point of the next
+    // step is loaded before the current one is classified, so its memory latency overlaps the work
+    static_assert(kChunk % kCertThreads == 0, "whole steps per chunk");
+    constexpr uint32_t kPerChunk = kChunk / kCertThreads;
+    const uint32_t steps = (last - first) * kPerChunk;
+    auto index_of = [&](uint32_t st) {
+      return (uint64_t)list[first + st / kPerChunk] * kChunk + (st % kPerChunk) * kCertThreads + warp * 32u + lane;
+    };
+    uint64_t i_next = steps ? index_of(0) : n;
+    uint4 p_next = i_next < n ? ld_stream16(pts + i_next) : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll 1
-      for (uint32_t k = warp * 32u; k < (uint32_t)kChunk; k += blockDim.x) {
-        const uint64_t i = base + k + lane;
+    for (uint32_t st = 0; st < steps; ++st) {
+      {
+        const uint64_t i = i_next;
         const bool valid = i < n;
-        const uint4 p = valid ? ld_stream16(pts + i) : make_uint4(0u, 0u, 0u, 0u);
+        const uint4 p = p_next;
+        if (st + 1 < steps) {
+          i_next = index_of(st + 1);
+          p_next = i_next < n ? ld_stream16(pts + i_next) : make_uint4(0u, 0u, 0u, 0u);
+        }
         bool defer = false;
         if (!kHq) {
           bool has = false;
