@@ -54,3 +54,58 @@ def test_lidar_100m_full_frame(gpu, lidar100m, transform):
         assert np.array_equal(got_acc[:, 1] & 0xFFFFFFFF, sb)
         assert np.array_equal(img_b.cpu().numpy().view(np.uint32), oracle.resolve_basic(ref))
         assert np.array_equal(img_h.cpu().numpy().view(np.uint32), oracle.resolve_hq((sr, sg, sb, cnt)))
+
+
+def test_lidar_100m_frame_from_host(gpu, lidar100m):
+    """The end-to-end path bench.py times (pcr_render_frame_host: chunked upload, both passes, both images
+    back to pinned host memory), at full size, against the oracle's images."""
+    import torch
+    pts = lidar100m
+    view = scenes.lidar_1km_view()
+    W, H = view.width, view.height
+    fb = gpu.pcr_create_framebuffer(W, H, gpu.PCR_FB_HQ)
+    host = torch.from_numpy(pts.view(np.int32)).pin_memory()
+    d_pts = torch.empty_like(host, device="cuda")
+    d_img = torch.empty(2 * W * H, dtype=torch.int32, device="cuda")
+    h_b = torch.empty(W * H, dtype=torch.int32, pin_memory=True)
+    h_h = torch.empty(W * H, dtype=torch.int32, pin_memory=True)
+    gpu.pcr_render_frame_host(fb, host, view, d_pts, d_img, h_b, h_h)
+    torch.cuda.synchronize()
+    ref = oracle.render_atomicmin(pts, view)
+    sums, ovf = oracle.hq_accumulate(pts, view, ref, 1, 100)
+    assert not ovf
+    assert np.array_equal(h_b.numpy().view(np.uint32), oracle.resolve_basic(ref))
+    assert np.array_equal(h_h.numpy().view(np.uint32), oracle.resolve_hq(sums))
+    assert gpu.pcr_get_device_status(fb) == gpu.PCR_OK
+
+
+def test_batched_64_views_20m_sampled(gpu):
+    """The batched workload bench.py times (20M LIDAR points, seed 3; 64 orbit poses, seed 3; 640x480 /
+    1920x1080 / 3840x2160), one graph-replayed frame per mode, sampled views against the oracle."""
+    import torch
+    n = 20_000_000
+    pts = scenes.lidar(n, 3)
+    dev = torch.from_numpy(pts.view(np.int32)).cuda()
+    views = scenes.orbit_views(64, 3)
+    stream = torch.cuda.Stream()
+    cloud = gpu.pcr_cloud_create(dev)
+    for hq, sample in ((False, (0, 1, 2, 31, 62, 63)), (True, (5, 40))):
+        fbs = [gpu.pcr_create_framebuffer(v.width, v.height, gpu.PCR_FB_HQ if hq else 0) for v in views]
+        outs = [torch.empty(v.width * v.height, dtype=torch.int32, device="cuda") for v in views]
+        batch = gpu.pcr_batch_create(cloud, fbs, outs, hq=hq, clear_after=True)
+        gpu.pcr_batch_set_views(batch, views)
+        gpu.pcr_batch_capture(batch, stream)
+        gpu.pcr_batch_launch(batch, stream)
+        stream.synchronize()
+        for k in sample:
+            ref = oracle.render_atomicmin(pts, views[k])
+            if hq:
+                sums, ovf = oracle.hq_accumulate(pts, views[k], ref, 1, 100)
+                assert not ovf
+                want = oracle.resolve_hq(sums)
+            else:
+                want = oracle.resolve_basic(ref)
+            assert np.array_equal(outs[k].cpu().numpy().view(np.uint32), want), (hq, k)
+        batch.close()
+        for fb in fbs:
+            fb.close()
