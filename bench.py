@@ -518,8 +518,9 @@ def run_serving(args):
     """Serving workload: 6 resident LIDAR clouds (10M, 25M, 50M, 100M, 200M, 500M points; seeds 10..15), a
     seeded Poisson request stream (mean gap 2 ms, seed 7), resolution uniform over 1280x720 / 1920x1080 /
     2560x1440 / 3840x2160, 70 % basic / 30 % HQ (eps 1 %), a seeded orbit pose per request. Served by
-    pcr_server (continuous batching, 4 streams, 64 views per frame, 16 GB framebuffer budget), and again by a
-    server that renders one request per frame on one stream. Latency = completion - submission (queueing
+    pcr_server (continuous batching, 4 streams, at most 64 views and 1e9 point-views per frame, 16 GB
+    framebuffer budget), by the same server without the point-view cap, and by a server that renders one
+    request per frame on one stream. Latency = completion - submission (queueing
     included). Sampled requests are re-rendered alone through the single-view entry points and compared."""
     import torch
     import scenes
@@ -550,8 +551,10 @@ def run_serving(args):
     warm_reqs = [(k % len(sizes), views[k], k % 3 == 0, k % ring) for k in range(max(args.warmup, 1) * 4)]
     sample = set(range(0, n_req, max(1, n_req // 40)))
     results = {}
-    for name, streams, per_frame in (("continuous_batching", 4, 64), ("one_request_per_frame", 1, 1)):
-        server = pcr.pcr_server_create(streams, per_frame, 16 << 30)
+    for name, streams, per_frame, cap in (("continuous_batching", 4, 64, 1_000_000_000),
+                                          ("continuous_batching_uncapped", 4, 64, 0),
+                                          ("one_request_per_frame", 1, 1, 0)):
+        server = pcr.pcr_server_create(streams, per_frame, 16 << 30, cap)
         cids = [pcr.pcr_server_add_cloud(server, c) for c in clouds]
         _serve_stream(pcr, server, cids, warm_reqs, [0.0] * len(warm_reqs), outs, None)
         kept = {i: None for i in sample} if name == "continuous_batching" else None

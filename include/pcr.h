@@ -324,6 +324,10 @@ typedef struct {
   int32_t streams;                   /* concurrent frames on the device, 1..16 */
   int32_t max_batch_views;           /* requests merged into one frame, 1..PCR_MAX_BATCH_VIEWS */
   uint64_t framebuffer_budget_bytes; /* device memory for the framebuffers of admitted requests (pooled) */
+  uint64_t max_frame_point_views;    /* work cap of a merged frame: the sum over its requests of their
+                                        cloud's point count (0: no cap). A frame always takes its first
+                                        request, so one larger request still runs, alone. Bounds how long
+                                        a frame holds its stream, hence the wait of requests behind it. */
 } pcr_server_config;
 
 typedef struct {

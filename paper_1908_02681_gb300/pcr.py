@@ -43,7 +43,7 @@ class pcr_tuning(ctypes.Structure):
 
 class pcr_server_config(ctypes.Structure):
     _fields_ = [("streams", ctypes.c_int32), ("max_batch_views", ctypes.c_int32),
-                ("framebuffer_budget_bytes", ctypes.c_uint64)]
+                ("framebuffer_budget_bytes", ctypes.c_uint64), ("max_frame_point_views", ctypes.c_uint64)]
 
 
 class pcr_request(ctypes.Structure):
@@ -460,8 +460,9 @@ class Server:
             pass
 
 
-def pcr_server_create(streams: int = 4, max_batch_views: int = 64, framebuffer_budget_bytes: int = 4 << 30) -> Server:
-    cfg = pcr_server_config(streams, max_batch_views, framebuffer_budget_bytes)
+def pcr_server_create(streams: int = 4, max_batch_views: int = 64, framebuffer_budget_bytes: int = 4 << 30,
+                      max_frame_point_views: int = 0) -> Server:
+    cfg = pcr_server_config(streams, max_batch_views, framebuffer_budget_bytes, max_frame_point_views)
     h = ctypes.c_void_p()
     _check(load().pcr_server_create(ctypes.byref(cfg), ctypes.byref(h)))
     return Server(h.value)

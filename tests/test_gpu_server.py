@@ -121,3 +121,27 @@ def test_small_budget_and_rejections(gpu):
     with pytest.raises(gpu.PcrError):
         gpu.pcr_server_submit(server, cid, fp64, outs[0])            # served views use the EXACT transform
     gpu.pcr_server_destroy(server)
+
+
+def test_frame_work_cap(gpu):
+    """max_frame_point_views: with a cap of 2.5 clouds' worth, no frame holds more than 2 requests, and a
+    cap below one request still runs each request (alone); the images do not change."""
+    import torch
+    pts = scenes.lidar(1_000_000, 24)
+    dev = _dev(pts)
+    torch.cuda.synchronize()
+    views = scenes.orbit_views(7, 25, resolutions=((320, 180), (160, 120)))
+    for cap, most in ((2_500_000, 2), (1000, 1)):
+        server = gpu.pcr_server_create(streams=1, max_batch_views=8, framebuffer_budget_bytes=256 << 20,
+                                       max_frame_point_views=cap)
+        cid = gpu.pcr_server_add_cloud(server, dev)
+        outs = [torch.empty(v.width * v.height, dtype=torch.int32, device="cuda") for v in views]
+        gpu.pcr_server_submit_many(server, [dict(cloud=cid, view=v, out=o, background_rgba=BG)
+                                            for v, o in zip(views, outs)])
+        done = _drain(gpu, server, len(views))
+        assert all(d["status"] == 0 for d in done)
+        assert max(d["batch_views"] for d in done) == most
+        for v, o in zip(views, outs):
+            assert bool((_single(gpu, dev, v, False) == o).all())
+        gpu.pcr_server_destroy(server)
+
