@@ -408,8 +408,8 @@ def run_ours(args, wl):
 
 
 def run_batched(args):
-    """Batched workload: 20M LIDAR points (seed 3), 64 seeded orbit poses at 640x480 / 1920x1080 / 3840x2160,
-    basic and HQ frames. Plain path: per view one render call and one resolve call (clearing). Batched: one
+    """Batched workload: 20M LIDAR points (seed 3), 64 seeded orbit poses at 640x480 / 1920x1080 / 3840x2160
+    (--views, --resolutions change both), basic and HQ frames. Plain path: per view one render call and one resolve call (clearing). Batched: one
     pcr_batch frame (chunk culling, one persistent launch per pass, one resolve) replayed from a CUDA graph.
     Both produce the same images (checked). value = point-views per second of the batched frame."""
     import torch
@@ -421,7 +421,9 @@ def run_batched(args):
     host = torch.empty((n, 4), dtype=torch.int32, pin_memory=True)
     scenes.lidar(n, 3, out=host)
     pts = host.cuda()
-    views = scenes.orbit_views(64, 3)
+    res = [tuple(int(x) for x in r.split("x")) for r in args.resolutions.split(",")]
+    nv = args.views
+    views = scenes.orbit_views(nv, 3, resolutions=res)
     stream = torch.cuda.Stream()
     results = {}
     for hq in (False, True):
@@ -462,19 +464,19 @@ def run_batched(args):
         visible = pcr.pcr_batch_visible_chunks(batch)
         mode = "hq" if hq else "basic"
         results[mode] = {"plain_ms": t_plain, "batched_ms": t_batch, "speedup": t_plain / t_batch,
-                         "point_views_per_s": 64 * n / (t_batch * 1e-3), "identical_images": same,
-                         "visible_chunk_fraction": sum(visible) / (64 * ((n + 1023) // 1024))}
+                         "point_views_per_s": nv * n / (t_batch * 1e-3), "identical_images": same,
+                         "visible_chunk_fraction": sum(visible) / (nv * ((n + 1023) // 1024))}
         batch.close()
         cloud.close()
         for fb in fbs:
             fb.close()
-    line = {"metric": "batched frame: point-views/s (64 views, 20M points), speedup vs one view per launch",
+    line = {"metric": f"batched frame: point-views/s ({nv} views, 20M points), speedup vs one view per launch",
             "value": results["basic"]["point_views_per_s"] / 1e9, "unit": "G point-views/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": results["basic"]["batched_ms"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
-            "config": {"workload": "LIDAR 20M points (seed 3), 64 orbit poses (seed 3), 640x480 / 1920x1080 / "
-                                   "3840x2160 cycling, basic and HQ (eps 1%)"},
+            "config": {"workload": f"LIDAR 20M points (seed 3), {nv} orbit poses (seed 3), "
+                                   f"{' / '.join(args.resolutions.split(','))} cycling, basic and HQ (eps 1%)"},
             "modes": results}
     print(json.dumps(line), flush=True)
 
@@ -614,9 +616,12 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=100_000_000)
     ap.add_argument("--reference-sample", type=int, default=20_000_000)
     ap.add_argument("--requests", type=int, default=2000, help="serving workload: number of requests")
+    ap.add_argument("--views", type=int, default=64, help="batched workload: number of orbit poses")
+    ap.add_argument("--resolutions", default="640x480,1920x1080,3840x2160",
+                    help="batched workload: resolutions cycled by pose index")
     ap.add_argument("--serving-scale", type=float, default=1.0, help="serving workload: cloud size factor")
     args = ap.parse_args()
-    if args.workload == "batched64":
+    if args.workload in ("batched", "batched64"):
         run_batched(args)
         return
     if args.workload == "serving":

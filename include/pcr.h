@@ -300,7 +300,7 @@ pcr_status pcr_batch_destroy(pcr_batch* batch);
  * hq, eps_num, eps_den, background_rgba, clear_after: as for pcr_batch_create. A larger n or count returns
  * PCR_ERR_INVALID_ARG, with the limit in pcr_last_error_message(), and enqueues nothing.
  *
- * The array takes about 7.4 MB on every device that loads libpcr, until the process exits. The first call
+ * The array takes about 3.4 MB on every device that loads libpcr, until the process exits. The first call
  * on each device looks up the array's address (cudaGetSymbolAddress) with that device current: make that
  * first call before any stream capture. All calls on a device share the one array, which keeps what the
  * last call left in it (each call clears what must start at zero). Calls whose work overlaps on the GPU

@@ -10,8 +10,9 @@
 //     the near plane, beyond the far plane, or at |ndc| > 1 + 1e-5, which the definition's float pixel
 //     mapping (relative error below 1e-6) sends outside the image. A box with a NaN or infinite bound is
 //     never skipped.
-//   * one persistent launch per pass for all views: work items are (view, run of kSlice visible chunks),
-//     pulled from a counter; a block reloads a view's depth table only when its view changes.
+//   * one persistent launch per pass for all views: work items are (range of kSlice consecutive chunks,
+//     view), taken range by range from a counter, so a range is read from HBM once for all views; a block
+//     reloads a view's depth table when its view changes.
 //   * one resolve launch for all views.
 #pragma once
 
@@ -20,7 +21,7 @@
 namespace pcr {
 
 constexpr int kChunk = 1024;        // points per chunk (bounding box granularity)
-constexpr int kSlice = 16;          // visible chunks per work item
+constexpr int kSlice = 16;          // consecutive chunks per work item
 constexpr int kMaxBatchViews = 256;
 
 // Per-view constants of a batch that live in device memory (read once per work item).
@@ -91,10 +92,11 @@ __global__ void __launch_bounds__(256) k_chunk_bounds(const uint4* __restrict__ 
 
 // ----------------------------------------------------------------------------------------------- culling
 
-// For each (view, chunk): append the chunk to the view's list unless its box is certainly culled.
-// Thread per chunk; the grid's y dimension is the view. One atomic per warp for the list position.
+// For each (view, chunk): bit c of the view's visibility mask is set unless chunk c's box is certainly
+// culled. Thread per chunk, one 32-bit mask word per warp (a ballot, no atomics); the grid's y dimension
+// is the view. counts[v] (zeroed before) receives the number of visible chunks.
 __global__ void __launch_bounds__(256) k_cull(const float* __restrict__ bounds, uint32_t n_chunks,
-                                              const BatchSlot* __restrict__ slots, uint32_t* __restrict__ lists,
+                                              const BatchSlot* __restrict__ slots, uint32_t* __restrict__ masks,
                                               uint32_t* __restrict__ counts) {
   const uint32_t v = blockIdx.y;
   const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -120,34 +122,24 @@ __global__ void __launch_bounds__(256) k_cull(const float* __restrict__ bounds, 
     keep = !culled;  // NaN bounds: every comparison false, never culled
   }
   const unsigned m = __ballot_sync(0xFFFFFFFFu, keep);
-  if (m == 0u) return;
-  const uint32_t lane = threadIdx.x & 31u;
-  uint32_t base = 0;
-  if (lane == 0) base = atomicAdd(counts + v, (uint32_t)__popc(m));
-  base = __shfl_sync(0xFFFFFFFFu, base, 0);
-  if (keep) lists[(uint64_t)v * n_chunks + base + __popc(m & ((1u << lane) - 1u))] = c;
+  const uint32_t words = (n_chunks + 31u) / 32u;
+  if ((threadIdx.x & 31u) == 0u && c / 32u < words) {
+    masks[(uint64_t)v * words + c / 32u] = m;
+    if (m) atomicAdd(counts + v, (uint32_t)__popc(m));
+  }
 }
 
-// Work items: item_start[v] = sum over earlier views of ceil(count / kSlice); item_start[count] = total.
-// One block; views <= kMaxBatchViews.
-__global__ void k_items(const uint32_t* __restrict__ counts, uint32_t n_views, uint32_t* __restrict__ item_start,
-                        uint32_t* __restrict__ next_item) {
-  if (threadIdx.x == 0) {
-    uint32_t s = 0;
-    for (uint32_t v = 0; v < n_views; ++v) {
-      item_start[v] = s;
-      s += (counts[v] + kSlice - 1) / kSlice;
-    }
-    item_start[n_views] = s;
-    next_item[0] = 0u;
-    next_item[1] = 0u;
-  }
+// Resets the two work-item counters (pass 1, pass 2) of a frame.
+__global__ void k_items(uint32_t* __restrict__ next_item) {
+  if (threadIdx.x < 2) next_item[threadIdx.x] = 0u;
 }
 
 // ------------------------------------------------------------------------------------------- batch passes
 
 // Pass 1 (kHq = false) or pass 2 (kHq = true) for every view of a batch, one persistent launch. Work item
-// = (view, up to kSlice chunks of the view's visible list); items are taken in order from next_item[kHq].
+// = (range r of kSlice consecutive chunks, view v), numbered r * n_views + v and taken in that order from
+// next_item[kHq]: the views of one range run close together in time, so the range's points come from HBM
+// once and from L2 for the other views. An item covers the range's chunks whose mask bit is set.
 // params: per-view CertParams in device memory (tier 2 and the FP64 arbiter read them there; tier 1 holds
 // its constants in registers for the item).
 template <bool kHq>
@@ -157,9 +149,7 @@ template <bool kHq>
 __global__ void __launch_bounds__(kCertThreads, PCR_BATCH_MIN_BLOCKS) k_batch_pass(const uint4* __restrict__ pts, uint64_t n,
                                                              const CertParams* __restrict__ params,
                                                              const BatchSlot* __restrict__ slots,
-                                                             const uint32_t* __restrict__ lists,
-                                                             const uint32_t* __restrict__ counts,
-                                                             const uint32_t* __restrict__ item_start, uint32_t n_views,
+                                                             const uint32_t* __restrict__ masks, uint32_t n_views,
                                                              uint32_t n_chunks, uint32_t* __restrict__ next_item,
                                                              uint32_t eps_num, uint32_t eps_den) {
   __shared__ long long sF[3 * kTableEntries];
@@ -167,16 +157,22 @@ __global__ void __launch_bounds__(kCertThreads, PCR_BATCH_MIN_BLOCKS) k_batch_pa
   __shared__ uint32_t s_item;
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   uint4* q = queue[warp];
-  const uint32_t total = item_start[n_views];
+  static_assert(32 % kSlice == 0, "a range's mask bits lie in one word");
+  const uint32_t words = (n_chunks + 31u) / 32u;
+  const uint32_t total = (n_chunks + kSlice - 1) / kSlice * n_views;
   uint32_t cur_view = 0xFFFFFFFFu;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(next_item + (kHq ? 1 : 0), 1u);
     __syncthreads();
     const uint32_t item = s_item;
     if (item >= total) break;
-    // view of the item: the last v with item_start[v] <= item (views are few: linear scan)
-    uint32_t v = 0;
-    while (v + 1 < n_views && item_start[v + 1] <= item) ++v;
+    const uint32_t r = item / n_views, v = item - r * n_views;
+    const uint32_t c0 = r * kSlice;
+    const uint32_t bits = (masks[(uint64_t)v * words + c0 / 32u] >> (c0 % 32u)) & ((1u << kSlice) - 1u);
+    if (bits == 0u) {  // nothing of this range is visible in this view (the same in every thread)
+      __syncthreads();
+      continue;
+    }
     if (v != cur_view) {
       const long long* src = &params[v].F[0][0];
       for (int i = threadIdx.x; i < 3 * kTableEntries; i += blockDim.x) sF[i] = src[i];
@@ -188,17 +184,15 @@ __global__ void __launch_bounds__(kCertThreads, PCR_BATCH_MIN_BLOCKS) k_batch_pa
     const BatchSlot& S = slots[v];
     unsigned long long* const keys = S.keys;
     unsigned long long* const accum = S.accum;
-    const uint32_t first = (item - item_start[v]) * kSlice;
-    const uint32_t last = min(first + (uint32_t)kSlice, counts[v]);
-    const uint32_t* list = lists + (uint64_t)v * n_chunks;
     uint32_t qn = 0;
     // the item's points as one sequence of steps (kChunk / kCertThreads per chunk); the point of the next
     // step is loaded before the current one is classified, so its memory latency overlaps the work
     static_assert(kChunk % kCertThreads == 0, "whole steps per chunk");
     constexpr uint32_t kPerChunk = kChunk / kCertThreads;
-    const uint32_t steps = (last - first) * kPerChunk;
-    auto index_of = [&](uint32_t st) {
-      return (uint64_t)list[first + st / kPerChunk] * kChunk + (st % kPerChunk) * kCertThreads + warp * 32u + lane;
+    const uint32_t steps = (uint32_t)__popc(bits) * kPerChunk;
+    auto index_of = [&](uint32_t st) {  // step st's chunk: the (st / kPerChunk + 1)-th set bit of the range
+      const uint32_t c = c0 + __fns(bits, 0u, (int)(st / kPerChunk) + 1);
+      return (uint64_t)c * kChunk + (st % kPerChunk) * kCertThreads + warp * 32u + lane;
     };
     uint64_t i_next = steps ? index_of(0) : n;
     uint4 p_next = i_next < n ? ld_stream16(pts + i_next) : make_uint4(0u, 0u, 0u, 0u);
