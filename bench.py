@@ -417,7 +417,7 @@ def run_batched(args):
     from paper_1908_02681_gb300 import pcr
     torch.cuda.set_device(0)
     pcr.load()
-    n = 20_000_000
+    n = args.points
     host = torch.empty((n, 4), dtype=torch.int32, pin_memory=True)
     scenes.lidar(n, 3, out=host)
     pts = host.cuda()
@@ -470,12 +470,13 @@ def run_batched(args):
         cloud.close()
         for fb in fbs:
             fb.close()
-    line = {"metric": f"batched frame: point-views/s ({nv} views, 20M points), speedup vs one view per launch",
+    line = {"metric": f"batched frame: point-views/s ({nv} views, {n // 1_000_000}M points), speedup vs one view per "
+                      f"launch",
             "value": results["basic"]["point_views_per_s"] / 1e9, "unit": "G point-views/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": results["basic"]["batched_ms"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
-            "config": {"workload": f"LIDAR 20M points (seed 3), {nv} orbit poses (seed 3), "
+            "config": {"workload": f"LIDAR {n // 1_000_000}M points (seed 3), {nv} orbit poses (seed 3), "
                                    f"{' / '.join(args.resolutions.split(','))} cycling, basic and HQ (eps 1%)"},
             "modes": results}
     print(json.dumps(line), flush=True)
@@ -617,6 +618,7 @@ def main():
     ap.add_argument("--reference-sample", type=int, default=20_000_000)
     ap.add_argument("--requests", type=int, default=2000, help="serving workload: number of requests")
     ap.add_argument("--views", type=int, default=64, help="batched workload: number of orbit poses")
+    ap.add_argument("--points", type=int, default=20_000_000, help="batched workload: cloud size")
     ap.add_argument("--resolutions", default="640x480,1920x1080,3840x2160",
                     help="batched workload: resolutions cycled by pose index")
     ap.add_argument("--serving-scale", type=float, default=1.0, help="serving workload: cloud size factor")

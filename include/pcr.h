@@ -256,12 +256,16 @@ pcr_status pcr_batch_create(pcr_cloud* cloud, pcr_framebuffer* const* fbs, uint3
  * Blocks until the previous frame has copied the earlier views to the device. */
 pcr_status pcr_batch_set_views(pcr_batch* batch, const pcr_view* views);
 
-/* Enqueues one frame on `stream`: copy the views' constants to the device; per view, skip the chunks
- * whose bounding box is certainly outside the view (behind the near plane, beyond the far plane, or at
- * |ndc| > 1 + 1e-5, with margins covering every rounding); pass 1 for all views in one persistent
- * launch; pass 2 (hq) likewise; resolve every framebuffer into its output (and clear it, see
- * pcr_batch_create). Framebuffer
- * contents equal those of pcr_render_atomicmin / pcr_render_hq_splat per view, bit for bit. */
+/* Enqueues one frame on `stream`:
+ *   - copy the views' constants to the device;
+ *   - per view, mark the chunks whose bounding box is certainly outside the view (behind the near plane,
+ *     beyond the far plane, or at |ndc| > 1 + 1e-5, with margins covering every rounding);
+ *   - pass 1 for all views in one persistent launch that skips those chunks and takes the chunk ranges in
+ *     turn for every view (so each range is read from HBM once), then pass 2 (hq) likewise. A frame of at
+ *     most 4 views, or of a cloud of at least 10^8 points, instead runs one single-view pass per view,
+ *     which is faster there (frames recorded by pcr_batch_capture always use the persistent launch);
+ *   - resolve every framebuffer into its output (and clear it, see pcr_batch_create).
+ * Framebuffer contents equal those of pcr_render_atomicmin / pcr_render_hq_splat per view, bit for bit. */
 pcr_status pcr_batch_render(pcr_batch* batch, pcr_stream_t stream);
 
 /* Records one frame (as pcr_batch_render) into a CUDA graph owned by the batch; pcr_batch_launch

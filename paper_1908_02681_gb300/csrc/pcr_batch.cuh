@@ -21,7 +21,7 @@
 namespace pcr {
 
 constexpr int kChunk = 1024;        // points per chunk (bounding box granularity)
-constexpr int kSlice = 16;          // consecutive chunks per work item
+constexpr int kSlice = 32;          // consecutive chunks per work item (one word of a view's mask)
 constexpr int kMaxBatchViews = 256;
 
 // Per-view constants of a batch that live in device memory (read once per work item).
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(kCertThreads, PCR_BATCH_MIN_BLOCKS) k_batch_pa
   __shared__ uint32_t s_item;
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   uint4* q = queue[warp];
-  static_assert(32 % kSlice == 0, "a range's mask bits lie in one word");
+  static_assert(kSlice == 32, "a range is one word of the view's mask");
   const uint32_t words = (n_chunks + 31u) / 32u;
   const uint32_t total = (n_chunks + kSlice - 1) / kSlice * n_views;
   uint32_t cur_view = 0xFFFFFFFFu;
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(kCertThreads, PCR_BATCH_MIN_BLOCKS) k_batch_pa
     if (item >= total) break;
     const uint32_t r = item / n_views, v = item - r * n_views;
     const uint32_t c0 = r * kSlice;
-    const uint32_t bits = (masks[(uint64_t)v * words + c0 / 32u] >> (c0 % 32u)) & ((1u << kSlice) - 1u);
+    const uint32_t bits = masks[(uint64_t)v * words + c0 / 32u];  // kSlice == 32: the whole word
     if (bits == 0u) {  // nothing of this range is visible in this view (the same in every thread)
       __syncthreads();
       continue;
@@ -190,11 +190,9 @@ __global__ void __launch_bounds__(kCertThreads, PCR_BATCH_MIN_BLOCKS) k_batch_pa
     static_assert(kChunk % kCertThreads == 0, "whole steps per chunk");
     constexpr uint32_t kPerChunk = kChunk / kCertThreads;
     const uint32_t steps = (uint32_t)__popc(bits) * kPerChunk;
-    auto index_of = [&](uint32_t st) {  // step st's chunk: the (st / kPerChunk + 1)-th set bit of the range
-      const uint32_t c = c0 + __fns(bits, 0u, (int)(st / kPerChunk) + 1);
-      return (uint64_t)c * kChunk + (st % kPerChunk) * kCertThreads + warp * 32u + lane;
-    };
-    uint64_t i_next = steps ? index_of(0) : n;
+    // the chunk of the next step and its part: visible chunks in increasing order (lowest remaining bit)
+    uint32_t rem = bits & (bits - 1u), nc = c0 + (uint32_t)(__ffs(bits) - 1), nk = 0;
+    uint64_t i_next = (uint64_t)nc * kChunk + warp * 32u + lane;
     uint4 p_next = i_next < n ? ld_stream16(pts + i_next) : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll 1
     for (uint32_t st = 0; st < steps; ++st) {
@@ -203,7 +201,12 @@ __global__ void __launch_bounds__(kCertThreads, PCR_BATCH_MIN_BLOCKS) k_batch_pa
         const bool valid = i < n;
         const uint4 p = p_next;
         if (st + 1 < steps) {
-          i_next = index_of(st + 1);
+          if (++nk == kPerChunk) {  // next visible chunk of the range (there is one: more steps remain)
+            nk = 0;
+            nc = c0 + (uint32_t)(__ffs(rem) - 1);
+            rem &= rem - 1u;
+          }
+          i_next = (uint64_t)nc * kChunk + nk * kCertThreads + warp * 32u + lane;
           p_next = i_next < n ? ld_stream16(pts + i_next) : make_uint4(0u, 0u, 0u, 0u);
         }
         bool defer = false;
