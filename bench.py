@@ -196,8 +196,9 @@ def run_reference(args, wl):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    # bounded work: at most about 400M point-frames over the whole run
-    sample_n = min(wl["n"], args.reference_sample, max(1_000_000, 400_000_000 // max(1, args.steps)))
+    # bounded work: at most about 3e9 point-frames over the whole run (about a minute at the default 600
+    # steps), so that the oracle's per-frame cost (clear and resolve of every pixel) stays small per point
+    sample_n = min(wl["n"], args.reference_sample, max(1_000_000, 3_000_000_000 // max(1, args.steps)))
     pts = np.empty((sample_n, 4), np.uint32)
     wl["gen"](sample_n, pts)
     for _ in range(args.warmup):
