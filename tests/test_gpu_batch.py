@@ -120,3 +120,23 @@ def test_batch_edge_cases(gpu):
     pview.ranges = [[0.0, 10.0, 1e9]]
     with pytest.raises(gpu.PcrError):
         gpu.pcr_batch_set_views(batch, [views[0], views[1], pview])
+
+
+def test_batch_maximum_view_count(gpu):
+    """PCR_MAX_BATCH_VIEWS (256) views in one frame, graph-captured: sampled views against the oracle; 257
+    views are refused."""
+    import torch
+    pts = scenes.lidar(500_001, 61)
+    dev = _dev(pts)
+    views = scenes.orbit_views(256, 61, resolutions=((32, 24), (48, 27), (40, 40)))
+    cloud, fbs, outs, batch = _frame(gpu, dev, views, False, clear_after=True)
+    stream = torch.cuda.Stream()
+    gpu.pcr_batch_capture(batch, stream)
+    gpu.pcr_batch_launch(batch, stream)
+    stream.synchronize()
+    for k in (0, 1, 127, 200, 255):
+        want = oracle.resolve_basic(oracle.render_atomicmin(pts, views[k]), 0x00112233)
+        assert np.array_equal(outs[k].cpu().numpy().view(np.uint32), want), k
+    extra = fbs + [gpu.pcr_create_framebuffer(32, 24)]
+    with pytest.raises(gpu.PcrError):
+        gpu.pcr_batch_create(cloud, extra, outs + [torch.empty(32 * 24, dtype=torch.int32, device="cuda")])

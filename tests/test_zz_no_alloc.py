@@ -71,3 +71,21 @@ def test_noalloc_rejects_sizes_beyond_the_array(gpu):
     st = lib.pcr_render_views_noalloc(ctypes.c_void_p(dev.data_ptr()), gpu.PCR_NOALLOC_MAX_POINTS + 1, fb_arr,
                                       out_arr, view_arr, 1, 0, 1, 100, 0, 1, None)
     assert st == gpu.PCR_ERR_INVALID_ARG and "points" in gpu.pcr_last_error_message()
+
+
+def test_noalloc_at_its_size_limits(gpu):
+    """Exactly PCR_NOALLOC_MAX_POINTS points and PCR_NOALLOC_MAX_VIEWS views: the same images as the
+    allocating batch entry point."""
+    import torch
+    n = gpu.PCR_NOALLOC_MAX_POINTS
+    host = torch.empty((n, 4), dtype=torch.int32, pin_memory=True)
+    scenes.lidar(n, 34, out=host)
+    dev = host.cuda()
+    views = scenes.orbit_views(gpu.PCR_NOALLOC_MAX_VIEWS, 34, resolutions=((320, 180), (256, 256)))
+    want = _with_batch(gpu, dev, views, False)
+    fbs = [gpu.pcr_create_framebuffer(v.width, v.height) for v in views]
+    outs = [torch.full((v.width * v.height,), -1, dtype=torch.int32, device="cuda") for v in views]
+    gpu.pcr_render_views_noalloc(dev, fbs, outs, views, background_rgba=BG)
+    torch.cuda.synchronize()
+    for k, (a, b) in enumerate(zip(outs, want)):
+        assert bool((a == b).all()), k
