@@ -214,7 +214,8 @@ pcr_status pcr_create_framebuffer(int32_t width, int32_t height, uint32_t flags,
     g_launches.fetch_add(1, std::memory_order_relaxed);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  // wait for the clear on the stream it ran on (not the whole device: other streams keep running)
+  if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
   if (e != cudaSuccess) {
     pcr_destroy_framebuffer(fb);
     return cuda_fail(e, "framebuffer clear");
