@@ -433,13 +433,20 @@ def run_batched(args):
         outs_plain = [torch.empty(v.width * v.height, dtype=torch.int32, device="cuda") for v in views]
         outs_batch = [torch.empty(v.width * v.height, dtype=torch.int32, device="cuda") for v in views]
 
-        def plain_frame():
-            for v, fb, o in zip(views, fbs, outs_plain):
+        def plain_frame(vs=views, outs=outs_plain):
+            for v, fb, o in zip(vs, fbs, outs):
                 if hq:
                     pcr.pcr_render_hq_splat(fb, pts, v, 1, 100, stream)
                 else:
                     pcr.pcr_render_atomicmin(fb, pts, v, stream)
                 pcr.pcr_resolve(fb, o, 0, True, stream)
+
+        # the plain path with the depth in FP64 as the paper computes it (PCR_TRANSFORM_FP64), one view
+        # per launch
+        views_fp64 = [scenes.View(v.view_proj, v.near, v.far, v.width, v.height) for v in views]
+        for v in views_fp64:
+            v.transform = 1
+        outs_fp64 = [torch.empty(v.width * v.height, dtype=torch.int32, device="cuda") for v in views]
 
         def timed(fn, steps):
             for _ in range(args.warmup):
@@ -455,16 +462,19 @@ def run_batched(args):
 
         with torch.cuda.stream(stream):
             t_plain = timed(plain_frame, max(2, args.steps // 4))
+            t_fp64 = timed(lambda: plain_frame(views_fp64, outs_fp64), 2)
             cloud = pcr.pcr_cloud_create(pts, stream)
             batch = pcr.pcr_batch_create(cloud, fbs, outs_batch, hq=hq, clear_after=True)
             pcr.pcr_batch_set_views(batch, views)
             pcr.pcr_batch_capture(batch, stream)
             t_batch = timed(lambda: pcr.pcr_batch_launch(batch, stream), args.steps)
             stream.synchronize()
-        same = all(bool((a == b).all()) for a, b in zip(outs_plain, outs_batch))
+        same = all(bool((a == b).all()) for a, b in zip(outs_plain, outs_batch)) and \
+            all(bool((a == b).all()) for a, b in zip(outs_fp64, outs_batch))
         visible = pcr.pcr_batch_visible_chunks(batch)
         mode = "hq" if hq else "basic"
         results[mode] = {"plain_ms": t_plain, "batched_ms": t_batch, "speedup": t_plain / t_batch,
+                         "plain_fp64_ms": t_fp64, "speedup_vs_plain_fp64": t_fp64 / t_batch,
                          "point_views_per_s": nv * n / (t_batch * 1e-3), "identical_images": same,
                          "visible_chunk_fraction": sum(visible) / (nv * ((n + 1023) // 1024))}
         batch.close()
@@ -592,6 +602,36 @@ def run_serving(args):
                 same += int(bool((alone == kept[i]).all()))
                 fb.close()
             results[name]["sampled_identical_to_alone"] = f"{same}/{len(kept)}"
+    # The plain path: each request rendered alone, one view per launch, the depth in FP64 as the paper
+    # computes it (PCR_TRANSFORM_FP64), back to back on one stream, over a sample of the same requests.
+    k_plain = min(n_req, 300)
+    fb_plain = {}
+
+    def plain_one(cloud, v, hq, out):
+        key = (v.width, v.height, hq)
+        if key not in fb_plain:
+            fb_plain[key] = pcr.pcr_create_framebuffer(v.width, v.height, pcr.PCR_FB_HQ if hq else 0)
+        fb = fb_plain[key]
+        vf = scenes.View(v.view_proj, v.near, v.far, v.width, v.height)
+        vf.transform = 1
+        if hq:
+            pcr.pcr_render_hq_splat(fb, clouds[cloud], vf, 1, 100)
+            pcr.pcr_resolve(fb, out, 0, True)
+        else:
+            pcr.pcr_render_atomicmin(fb, clouds[cloud], vf)
+            pcr.pcr_resolve_basic(fb, out, 0, True)
+
+    for cloud, v, hq, slot in warm_reqs:
+        plain_one(cloud, v, hq, outs[(v.width, v.height)][slot])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for cloud, v, hq, slot in reqs[:k_plain]:
+        plain_one(cloud, v, hq, outs[(v.width, v.height)][slot])
+    torch.cuda.synchronize()
+    results["plain_fp64_one_view_per_launch"] = {"saturated_frames_per_s": k_plain / (time.perf_counter() - t0),
+                                                 "sample_requests": k_plain}
+    for fb in fb_plain.values():
+        fb.close()
     cb, one = results["continuous_batching"], results["one_request_per_frame"]
     line = {"metric": "served frames/s and latency (Poisson 2 ms mean gap, 6 resident clouds)",
             "value": cb["frames_per_s"], "unit": "frames/s", "n_gpus": 1, "steps": n_req, "warmup": len(warm_reqs),
@@ -601,6 +641,8 @@ def run_serving(args):
                                    f"{n_req} requests, Poisson mean gap 2 ms (seed 7), 720p-4K, 70% basic / 30% HQ"},
             "p50_ms": cb["p50_ms"], "p99_ms": cb["p99_ms"], "modes": results,
             "saturated_speedup_vs_one_request_per_frame": cb["saturated_frames_per_s"] / one["saturated_frames_per_s"],
+            "saturated_speedup_vs_plain_fp64": cb["saturated_frames_per_s"] /
+            results["plain_fp64_one_view_per_launch"]["saturated_frames_per_s"],
             "clocks": cb["clocks"]}
     print(json.dumps(line), flush=True)
 
