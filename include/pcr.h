@@ -243,8 +243,8 @@ pcr_status pcr_cloud_destroy(pcr_cloud* cloud);
  * and resolves into d_outs[i] (caller-owned device memory, width * height u32 of fbs[i]). hq != 0 makes it
  * a high-quality splatting frame (every fbs[i] created with PCR_FB_HQ; eps_num / eps_den as in
  * pcr_render_hq_splat). The framebuffers must be distinct, cleared, on the cloud's device, and used by
- * nothing else while the batch exists. The batch owns its device workspace (per-view constants, visible
- * chunk lists: 4 B per chunk per view) and a pinned staging buffer for the views. clear_after != 0: every
+ * nothing else while the batch exists. The batch owns its device workspace (per-view constants, chunk
+ * visibility masks: 1 bit per chunk per view) and a pinned staging buffer for the views. clear_after != 0: every
  * frame clears the framebuffers after resolving them (ready for the next frame); 0 leaves keys and sums in
  * place (pcr_framebuffer_keys reads them; clear before the next frame). */
 pcr_status pcr_batch_create(pcr_cloud* cloud, pcr_framebuffer* const* fbs, uint32_t* const* d_outs, int32_t count,
@@ -290,9 +290,9 @@ pcr_status pcr_batch_destroy(pcr_batch* batch);
 #define PCR_NOALLOC_MAX_VIEWS 8
 #define PCR_NOALLOC_MAX_POINTS 134217728ull /* 2^27 points (131072 chunks of 1024) */
 
-/* One batched frame of count views of n points: the same kernels and the same images as
- * pcr_cloud_create + pcr_batch_create + pcr_batch_set_views + pcr_batch_render, but the frame's workspace
- * (chunk bounds, visible lists, per-view constants, counters) is a fixed device array inside libpcr, so
+/* One batched frame of count views of n points: the same images as pcr_cloud_create + pcr_batch_create +
+ * pcr_batch_set_views + pcr_batch_render (always with the batched persistent launch), but the frame's
+ * workspace (chunk bounds, visibility masks, per-view constants, counters) is a fixed device array inside libpcr, so
  * the call allocates nothing: no cudaMalloc, cudaFree or other allocating routine. It is meant for callers
  * that must not allocate while they render: a render loop in which a cudaMalloc or cudaFree would
  * synchronise the device and stall other streams; a process held to a fixed device-memory budget or to
