@@ -995,23 +995,40 @@ inline void raster_launch(const uint4* pts, uint64_t n, const CertParams& P, uns
     raster_launch3<kApprox, kMerge, false>(pts, n, P, keys, nullptr, status, sms, per_sm, s);
 }
 
+// The certified constants of a view, prepared on this thread and kept for the next call with the same view
+// and mode (prepare_cert builds a 12 KB exact table: ~14 us of host time per call). Returns false when the
+// view is outside the single-precision preconditions.
+inline bool cached_cert(const DevView& v, bool approximate, const CertParams** out) {
+  static thread_local CertParams P;
+  static thread_local DevView last_v;
+  static thread_local int last = -1;  // -1: nothing cached; else approximate (0/1) of the cached view
+  static thread_local bool last_ok = false;
+  if (last != (approximate ? 1 : 0) || std::memcmp(&last_v, &v, sizeof(DevView)) != 0) {
+    last_ok = host::prepare_cert(v, approximate, &P);
+    std::memcpy(&last_v, &v, sizeof(DevView));
+    last = approximate ? 1 : 0;
+  }
+  *out = &P;
+  return last_ok;
+}
+
 // Pass 1 for a view with n >= 1 points. status: the framebuffer's status word (timeout bit).
 inline bool launch_raster_certified(const uint4* pts, uint64_t n, const DevView& v, bool approximate,
                                     unsigned long long* keys, uint32_t* status, int sms, cudaStream_t s,
                                     unsigned long long* stats = nullptr, const Tuning& t = Tuning()) {
-  static thread_local CertParams P;  // 12.8 KB: kept off the stack
+  const CertParams* Pp = nullptr;
   const unsigned grid = cert_grid(n, sms, t.blocks_per_sm);
-  if (!host::prepare_cert(v, approximate, &P)) {
+  if (!cached_cert(v, approximate, &Pp)) {
     k_raster_fp64<<<grid, 256, 0, s>>>(pts, n, v, keys);
     return true;
   }
   const int b = t.blocks_per_sm;
   if (approximate)
-    t.merge ? raster_launch<true, true>(pts, n, P, keys, stats, status, sms, b, s)
-            : raster_launch<true, false>(pts, n, P, keys, stats, status, sms, b, s);
+    t.merge ? raster_launch<true, true>(pts, n, *Pp, keys, stats, status, sms, b, s)
+            : raster_launch<true, false>(pts, n, *Pp, keys, stats, status, sms, b, s);
   else
-    t.merge ? raster_launch<false, true>(pts, n, P, keys, stats, status, sms, b, s)
-            : raster_launch<false, false>(pts, n, P, keys, stats, status, sms, b, s);
+    t.merge ? raster_launch<false, true>(pts, n, *Pp, keys, stats, status, sms, b, s)
+            : raster_launch<false, false>(pts, n, *Pp, keys, stats, status, sms, b, s);
   return true;
 }
 
@@ -1029,19 +1046,19 @@ inline bool launch_hq_certified(const uint4* pts, uint64_t n, const DevView& v, 
                                 const unsigned long long* keys, unsigned long long* accum, uint32_t eps_num,
                                 uint32_t eps_den, uint32_t* status, int sms, cudaStream_t s,
                                 const Tuning& t = Tuning()) {
-  static thread_local CertParams P;
+  const CertParams* Pp = nullptr;
   const unsigned grid = cert_grid(n, sms, t.blocks_per_sm);
-  if (!host::prepare_cert(v, approximate, &P)) {
+  if (!cached_cert(v, approximate, &Pp)) {
     k_hq_fp64<<<grid, 256, 0, s>>>(pts, n, v, keys, accum, eps_num, eps_den);
     return true;
   }
   const int b = t.blocks_per_sm;
   if (approximate)
-    t.merge ? hq_launch<true, true>(pts, n, P, keys, accum, eps_num, eps_den, status, sms, b, s)
-            : hq_launch<true, false>(pts, n, P, keys, accum, eps_num, eps_den, status, sms, b, s);
+    t.merge ? hq_launch<true, true>(pts, n, *Pp, keys, accum, eps_num, eps_den, status, sms, b, s)
+            : hq_launch<true, false>(pts, n, *Pp, keys, accum, eps_num, eps_den, status, sms, b, s);
   else
-    t.merge ? hq_launch<false, true>(pts, n, P, keys, accum, eps_num, eps_den, status, sms, b, s)
-            : hq_launch<false, false>(pts, n, P, keys, accum, eps_num, eps_den, status, sms, b, s);
+    t.merge ? hq_launch<false, true>(pts, n, *Pp, keys, accum, eps_num, eps_den, status, sms, b, s)
+            : hq_launch<false, false>(pts, n, *Pp, keys, accum, eps_num, eps_den, status, sms, b, s);
   return true;
 }
 
