@@ -22,6 +22,11 @@ struct pcr_framebuffer {
   ulonglong2* accum;         // width * height (HQ only)
   uint32_t* status;          // device status word
   pcr::Tuning tuning;        // launch tuning of the point passes
+  // device copy of the depth table of the view last rendered with the certified transform (loaded by the
+  // passes with coalesced reads), re-uploaded when the view changes
+  long long* d_table;
+  pcr::DevView table_view;
+  bool table_valid;
   // frames from host memory (pcr_render_frame_host): copy stream and events, created by its first call
   cudaStream_t copy_stream;
   cudaEvent_t copy_events[9];  // [0]: start of the frame on the caller's stream; [1..8]: chunk k landed
@@ -147,6 +152,25 @@ pcr_status after_launch(const char* what, uint64_t launches = 1) {
   return e == cudaSuccess ? PCR_OK : cuda_fail(e, what);
 }
 
+// The device copy of the view's depth table for the certified passes on fb (uploaded on `s` when the view
+// differs from the last one), or null (double-float transform, FP64 kernels, or the upload failed: the
+// passes then read the table from their parameter block).
+const long long* fb_table(pcr_framebuffer* fb, const pcr::DevView& dv, int transform, cudaStream_t s) {
+  if (transform != PCR_TRANSFORM_EXACT) return nullptr;
+  const pcr::CertParams* P = nullptr;
+  if (!pcr::cached_cert(dv, false, &P)) return nullptr;
+  if (!fb->table_valid || std::memcmp(&fb->table_view, &dv, sizeof(dv)) != 0) {
+    fb->table_valid = false;
+    if (cudaMemcpyAsync(fb->d_table, &P->F[0][0], sizeof(P->F), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    fb->table_view = dv;
+    fb->table_valid = true;
+  }
+  return fb->d_table;
+}
+
 // Launches pass 1 (atomic minimum) for a validated view.
 pcr_status launch_raster(pcr_framebuffer* fb, const pcr_point* d_points, uint64_t n, const pcr::DevView& dv,
                          int transform, cudaStream_t s, unsigned long long* stats = nullptr) {
@@ -155,8 +179,9 @@ pcr_status launch_raster(pcr_framebuffer* fb, const pcr_point* d_points, uint64_
     pcr::k_raster_fp64<<<grid_for(n, 256, fb->device, 8), 256, 0, s>>>(pts, n, dv, fb->keys);
     return after_launch("k_raster_fp64");
   }
+  const long long* table = fb_table(fb, dv, transform, s);
   return pcr::launch_raster_certified(pts, n, dv, transform == PCR_TRANSFORM_DOUBLE_FLOAT, fb->keys, fb->status,
-                                      sm_count(fb->device), s, stats, fb->tuning)
+                                      sm_count(fb->device), s, stats, fb->tuning, table)
              ? after_launch("k_raster_certified")
              : fail(PCR_ERR_CUDA, "certified raster launch failed");
 }
@@ -169,8 +194,9 @@ pcr_status launch_hq(pcr_framebuffer* fb, const pcr_point* d_points, uint64_t n,
     pcr::k_hq_fp64<<<grid_for(n, 256, fb->device, 8), 256, 0, s>>>(pts, n, dv, fb->keys, acc, eps_num, eps_den);
     return after_launch("k_hq_fp64");
   }
+  const long long* table = fb_table(fb, dv, transform, s);
   return pcr::launch_hq_certified(pts, n, dv, transform == PCR_TRANSFORM_DOUBLE_FLOAT, fb->keys, acc, eps_num,
-                                  eps_den, fb->status, sm_count(fb->device), s, fb->tuning)
+                                  eps_den, fb->status, sm_count(fb->device), s, fb->tuning, table)
              ? after_launch("k_hq_certified")
              : fail(PCR_ERR_CUDA, "certified HQ launch failed");
 }
@@ -199,11 +225,13 @@ pcr_status pcr_create_framebuffer(int32_t width, int32_t height, uint32_t flags,
   e = cudaMalloc(&fb->keys, npx * sizeof(unsigned long long));
   if (e == cudaSuccess && (flags & PCR_FB_HQ)) e = cudaMalloc(&fb->accum, npx * sizeof(ulonglong2));
   if (e == cudaSuccess) e = cudaMalloc(&fb->status, 256);
+  if (e == cudaSuccess) e = cudaMalloc(&fb->d_table, sizeof(pcr::CertParams::F));
   if (e != cudaSuccess) {
     cudaGetLastError();
     cudaFree(fb->keys);
     cudaFree(fb->accum);
     cudaFree(fb->status);
+    cudaFree(fb->d_table);
     delete fb;
     return e == cudaErrorMemoryAllocation ? fail(PCR_ERR_OOM, "cudaMalloc of %llu pixels failed", (unsigned long long)npx)
                                           : cuda_fail(e, "cudaMalloc");
@@ -233,6 +261,7 @@ pcr_status pcr_destroy_framebuffer(pcr_framebuffer* fb) {
   cudaFree(fb->keys);
   cudaFree(fb->accum);
   cudaFree(fb->status);
+  cudaFree(fb->d_table);
   if (fb->copy_stream) {
     cudaStreamDestroy(fb->copy_stream);
     for (cudaEvent_t e : fb->copy_events) cudaEventDestroy(e);

@@ -575,6 +575,17 @@ __device__ __forceinline__ void load_table(const CertParams& P, long long* sF) {
   __syncthreads();
 }
 
+// The same table from a device-memory copy (coalesced loads; from the kernel parameter block, every lane
+// reading its own address, the copy took ~14 us per launch). table == null: from the parameter block.
+__device__ __forceinline__ void load_table(const CertParams& P, const long long* __restrict__ table, long long* sF) {
+  if (table == nullptr) {
+    load_table(P, sF);
+    return;
+  }
+  for (int i = threadIdx.x; i < 3 * kTableEntries; i += blockDim.x) sF[i] = table[i];
+  __syncthreads();
+}
+
 #ifndef PCR_CERT_MIN_BLOCKS
 #define PCR_CERT_MIN_BLOCKS 6
 #endif
@@ -752,7 +763,8 @@ __device__ __forceinline__ void defer_points(bool defer, const uint4& p, uint4* 
 template <bool kApprox, bool kMerge, bool kStats>
 __global__ void __launch_bounds__(kCertThreads, PCR_CERT_MIN_BLOCKS) k_raster_cert(
     const uint4* __restrict__ pts, uint64_t n, const __grid_constant__ CertParams P,
-    unsigned long long* __restrict__ keys, unsigned long long* __restrict__ stats, uint32_t* __restrict__ status) {
+    unsigned long long* __restrict__ keys, unsigned long long* __restrict__ stats, uint32_t* __restrict__ status,
+    const long long* __restrict__ table) {
   __shared__ long long sF[3 * kTableEntries];
   __shared__ uint4 queue[kCertWarps][kQueue];
   __shared__ __align__(128) uint4 ring[kCertWarps][2][kTile];
@@ -760,7 +772,7 @@ __global__ void __launch_bounds__(kCertThreads, PCR_CERT_MIN_BLOCKS) k_raster_ce
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   if (lane == 0) ring_init(bars[warp]);
   __syncwarp();
-  if (!kApprox) load_table(P, sF);
+  if (!kApprox) load_table(P, table, sF);
   uint4* q = queue[warp];
   uint32_t qn = 0;
   unsigned c_exact = 0, c_amb = 0, c_fp64 = 0, c_defer = 0;
@@ -881,7 +893,7 @@ template <bool kApprox, bool kMerge>
 __global__ void __launch_bounds__(kCertThreads, PCR_HQ_MIN_BLOCKS) k_hq_cert(
     const uint4* __restrict__ pts, uint64_t n, const __grid_constant__ CertParams P,
     const unsigned long long* __restrict__ keys, unsigned long long* __restrict__ accum, uint32_t eps_num,
-    uint32_t eps_den, uint32_t* __restrict__ status) {
+    uint32_t eps_den, uint32_t* __restrict__ status, const long long* __restrict__ table) {
   __shared__ long long sF[3 * kTableEntries];
   __shared__ uint4 queue[kCertWarps][kQueue];
   __shared__ __align__(128) uint4 ring[kCertWarps][2][kTile];
@@ -889,7 +901,7 @@ __global__ void __launch_bounds__(kCertThreads, PCR_HQ_MIN_BLOCKS) k_hq_cert(
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   if (lane == 0) ring_init(bars[warp]);
   __syncwarp();
-  if (!kApprox) load_table(P, sF);
+  if (!kApprox) load_table(P, table, sF);
   uint4* q = queue[warp];
   uint32_t qn = 0;
   // the two points of a tile are classified together so that their stored-key reads overlap
@@ -978,21 +990,24 @@ inline unsigned persistent_grid(int resident, uint64_t n, int sms, int per_sm) {
   return cert_grid(n, sms, per_sm < resident ? per_sm : resident);
 }
 
+// table: device copy of P.F (or null: the kernels read it from the parameter block).
 template <bool kApprox, bool kMerge, bool kStats>
 inline void raster_launch3(const uint4* pts, uint64_t n, const CertParams& P, unsigned long long* keys,
-                           unsigned long long* stats, uint32_t* status, int sms, int per_sm, cudaStream_t s) {
+                           unsigned long long* stats, uint32_t* status, int sms, int per_sm, cudaStream_t s,
+                           const long long* table) {
   static const int resident = resident_blocks(k_raster_cert<kApprox, kMerge, kStats>);  // one per instantiation
   const unsigned grid = persistent_grid(resident, n, sms, per_sm);
-  k_raster_cert<kApprox, kMerge, kStats><<<grid, kCertThreads, 0, s>>>(pts, n, P, keys, stats, status);
+  k_raster_cert<kApprox, kMerge, kStats><<<grid, kCertThreads, 0, s>>>(pts, n, P, keys, stats, status, table);
 }
 
 template <bool kApprox, bool kMerge>
 inline void raster_launch(const uint4* pts, uint64_t n, const CertParams& P, unsigned long long* keys,
-                          unsigned long long* stats, uint32_t* status, int sms, int per_sm, cudaStream_t s) {
+                          unsigned long long* stats, uint32_t* status, int sms, int per_sm, cudaStream_t s,
+                          const long long* table = nullptr) {
   if (stats && !kApprox && !kMerge)
-    raster_launch3<false, false, true>(pts, n, P, keys, stats, status, sms, per_sm, s);
+    raster_launch3<false, false, true>(pts, n, P, keys, stats, status, sms, per_sm, s, table);
   else
-    raster_launch3<kApprox, kMerge, false>(pts, n, P, keys, nullptr, status, sms, per_sm, s);
+    raster_launch3<kApprox, kMerge, false>(pts, n, P, keys, nullptr, status, sms, per_sm, s, table);
 }
 
 // The certified constants of a view, prepared on this thread and kept for the next call with the same view
@@ -1015,7 +1030,8 @@ inline bool cached_cert(const DevView& v, bool approximate, const CertParams** o
 // Pass 1 for a view with n >= 1 points. status: the framebuffer's status word (timeout bit).
 inline bool launch_raster_certified(const uint4* pts, uint64_t n, const DevView& v, bool approximate,
                                     unsigned long long* keys, uint32_t* status, int sms, cudaStream_t s,
-                                    unsigned long long* stats = nullptr, const Tuning& t = Tuning()) {
+                                    unsigned long long* stats = nullptr, const Tuning& t = Tuning(),
+                                    const long long* table = nullptr) {
   const CertParams* Pp = nullptr;
   const unsigned grid = cert_grid(n, sms, t.blocks_per_sm);
   if (!cached_cert(v, approximate, &Pp)) {
@@ -1024,28 +1040,28 @@ inline bool launch_raster_certified(const uint4* pts, uint64_t n, const DevView&
   }
   const int b = t.blocks_per_sm;
   if (approximate)
-    t.merge ? raster_launch<true, true>(pts, n, *Pp, keys, stats, status, sms, b, s)
-            : raster_launch<true, false>(pts, n, *Pp, keys, stats, status, sms, b, s);
+    t.merge ? raster_launch<true, true>(pts, n, *Pp, keys, stats, status, sms, b, s, table)
+            : raster_launch<true, false>(pts, n, *Pp, keys, stats, status, sms, b, s, table);
   else
-    t.merge ? raster_launch<false, true>(pts, n, *Pp, keys, stats, status, sms, b, s)
-            : raster_launch<false, false>(pts, n, *Pp, keys, stats, status, sms, b, s);
+    t.merge ? raster_launch<false, true>(pts, n, *Pp, keys, stats, status, sms, b, s, table)
+            : raster_launch<false, false>(pts, n, *Pp, keys, stats, status, sms, b, s, table);
   return true;
 }
 
 template <bool kApprox, bool kMerge>
 inline void hq_launch(const uint4* pts, uint64_t n, const CertParams& P, const unsigned long long* keys,
                       unsigned long long* accum, uint32_t eps_num, uint32_t eps_den, uint32_t* status, int sms,
-                      int per_sm, cudaStream_t s) {
+                      int per_sm, cudaStream_t s, const long long* table = nullptr) {
   static const int resident = resident_blocks(k_hq_cert<kApprox, kMerge>);  // one per instantiation
   const unsigned grid = persistent_grid(resident, n, sms, per_sm);
-  k_hq_cert<kApprox, kMerge><<<grid, kCertThreads, 0, s>>>(pts, n, P, keys, accum, eps_num, eps_den, status);
+  k_hq_cert<kApprox, kMerge><<<grid, kCertThreads, 0, s>>>(pts, n, P, keys, accum, eps_num, eps_den, status, table);
 }
 
 // Pass 2 for a view with n >= 1 points. status: the framebuffer's status word (timeout bit).
 inline bool launch_hq_certified(const uint4* pts, uint64_t n, const DevView& v, bool approximate,
                                 const unsigned long long* keys, unsigned long long* accum, uint32_t eps_num,
                                 uint32_t eps_den, uint32_t* status, int sms, cudaStream_t s,
-                                const Tuning& t = Tuning()) {
+                                const Tuning& t = Tuning(), const long long* table = nullptr) {
   const CertParams* Pp = nullptr;
   const unsigned grid = cert_grid(n, sms, t.blocks_per_sm);
   if (!cached_cert(v, approximate, &Pp)) {
@@ -1054,11 +1070,11 @@ inline bool launch_hq_certified(const uint4* pts, uint64_t n, const DevView& v, 
   }
   const int b = t.blocks_per_sm;
   if (approximate)
-    t.merge ? hq_launch<true, true>(pts, n, *Pp, keys, accum, eps_num, eps_den, status, sms, b, s)
-            : hq_launch<true, false>(pts, n, *Pp, keys, accum, eps_num, eps_den, status, sms, b, s);
+    t.merge ? hq_launch<true, true>(pts, n, *Pp, keys, accum, eps_num, eps_den, status, sms, b, s, table)
+            : hq_launch<true, false>(pts, n, *Pp, keys, accum, eps_num, eps_den, status, sms, b, s, table);
   else
-    t.merge ? hq_launch<false, true>(pts, n, *Pp, keys, accum, eps_num, eps_den, status, sms, b, s)
-            : hq_launch<false, false>(pts, n, *Pp, keys, accum, eps_num, eps_den, status, sms, b, s);
+    t.merge ? hq_launch<false, true>(pts, n, *Pp, keys, accum, eps_num, eps_den, status, sms, b, s, table)
+            : hq_launch<false, false>(pts, n, *Pp, keys, accum, eps_num, eps_den, status, sms, b, s, table);
   return true;
 }
 
