@@ -485,7 +485,7 @@ def run_batched(args):
                       f"launch",
             "value": results["basic"]["point_views_per_s"] / 1e9, "unit": "G point-views/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": results["basic"]["batched_ms"],
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64+f64",
             "data": "synthetic",
             "config": {"workload": f"LIDAR {n // 1_000_000}M points (seed 3), {nv} orbit poses (seed 3), "
                                    f"{' / '.join(args.resolutions.split(','))} cycling, basic and HQ (eps 1%)"},
@@ -636,7 +636,7 @@ def run_serving(args):
     line = {"metric": "served frames/s and latency (Poisson 2 ms mean gap, 6 resident clouds)",
             "value": cb["frames_per_s"], "unit": "frames/s", "n_gpus": 1, "steps": n_req, "warmup": len(warm_reqs),
             "ms_per_step": 1e3 / cb["frames_per_s"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32+i64+f64", "data": "synthetic",
             "config": {"workload": f"serving: clouds {[n // 1_000_000 for n in sizes]}M LIDAR points (seeds 10-15), "
                                    f"{n_req} requests, Poisson mean gap 2 ms (seed 7), 720p-4K, 70% basic / 30% HQ"},
             "p50_ms": cb["p50_ms"], "p99_ms": cb["p99_ms"], "modes": results,
