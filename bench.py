@@ -372,7 +372,7 @@ def run_ours(args, wl):
         "metric": METRIC, "value": job_rate(n, world, ms_step) / 1e9, "unit": "Gpts/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"exact": "f32+f64", "fp64": "f64", "double-float": "f32"}[args.transform],
+        "dtype": {"exact": "f32+i64+f64", "fp64": "f64", "double-float": "f32"}[args.transform],
         "data": "synthetic",
         "config": {"workload": wl["desc"], "points": n, "width": W, "height": H, "transform": args.transform,
                    "step": "atomicMin pass + basic resolve + HQ band pass + HQ resolve with clear",
