@@ -102,7 +102,9 @@ typedef struct {
 #define PCR_FB_HQ 1u /* also allocate the 16 B/pixel HQ accumulation buffer (needed by pcr_render_hq_splat) */
 
 /* Allocates a width x height framebuffer on the current device (keys: 8 B/pixel; with PCR_FB_HQ also
- * sums: 16 B/pixel) and clears it (synchronously). width, height in 1..16384. */
+ * sums: 16 B/pixel; plus a 12 KB device copy of the depth table of the view last rendered, re-uploaded on
+ * the render call's stream when the view changes) and clears it (synchronously). width, height in
+ * 1..16384. */
 pcr_status pcr_create_framebuffer(int32_t width, int32_t height, uint32_t flags, pcr_framebuffer** out);
 
 /* Frees the framebuffer (synchronises the device first). NULL is accepted. */
