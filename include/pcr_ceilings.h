@@ -26,6 +26,28 @@ int pcr_ceiling_random_atomics(uint64_t* d_slots, uint32_t n_slots, uint64_t n_o
  * optimised away). d_sink must hold sms * 64 * 256 u32. */
 int pcr_ceiling_stream_read(const void* d_src, uint64_t n16, uint32_t* d_sink, void* stream);
 
+/* The framebuffer operations of the two passes for one view, without the per-point transform: the
+ * memory-side floor of Sections 2.1 and 2.2 for the access pattern of that cloud and view.
+ *
+ * pcr_ceiling_pattern_project writes, for each of the n points (16-B aligned, the rasterizer's layout),
+ * d_pix[i] = its pixel (row * width + column) or 0xFFFFFFFF when the FP64 definition culls it, and
+ * d_key[i] = its key (40-bit linear depth code << 24 | RGB) or all ones. m12 = rows 0, 1 and 3 of the
+ * row-major view-projection; 0 < near < far; width, height in 1..16384.
+ *
+ * pcr_ceiling_pattern_min does one 64-bit atomic minimum into d_keys[d_pix[i]] per visible fragment
+ * (pass 1); with filter = 1 a fragment first reads d_keys[d_pix[i]] and skips the atomic unless its key
+ * is smaller (the same minima: a stored key only decreases). pcr_ceiling_pattern_hq reads d_keys[d_pix[i]] per visible fragment and, when the fragment's
+ * code lies in the band eps_den * (q - qmin) <= eps_num * (qmin + nq), adds its colour and a count to
+ * d_accum[2 p], d_accum[2 p + 1] (pass 2; the sums layout of the framebuffer). Both read 12 B per point
+ * and take the points in order, 32 consecutive points per warp step. d_keys: width * height u64;
+ * d_accum: 2 * width * height u64. */
+int pcr_ceiling_pattern_project(const void* d_points, uint64_t n, const double* m12, double near_, double far_,
+                                int32_t width, int32_t height, uint32_t* d_pix, uint64_t* d_key, void* stream);
+int pcr_ceiling_pattern_min(const uint32_t* d_pix, const uint64_t* d_key, uint64_t n, uint64_t* d_keys, int32_t filter,
+                            void* stream);
+int pcr_ceiling_pattern_hq(const uint32_t* d_pix, const uint64_t* d_key, uint64_t n, const uint64_t* d_keys,
+                           uint64_t* d_accum, uint32_t eps_num, uint32_t eps_den, uint64_t nq, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,4 +1,5 @@
-// Roofline probes (include/pcr_ceilings.h): random u64 L2 atomics and 16-byte streaming reads.
+// Roofline probes (include/pcr_ceilings.h): random u64 L2 atomics, 16-byte streaming reads, and the passes'
+// framebuffer operations replayed without the transform.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -39,6 +40,55 @@ __global__ void __launch_bounds__(256) k_stream_read(const uint4* __restrict__ s
   if (acc == 0x9E3779B9u) sink[(uint64_t)blockIdx.x * blockDim.x + threadIdx.x] = acc;
 }
 
+// The visible fragments of a view in the order of the points: pixel (0xFFFFFFFF when culled) and key, by
+// the FP64 definition with linear depth. Run once, outside any timed region.
+__global__ void __launch_bounds__(256) k_pattern_project(const uint4* __restrict__ pts, uint64_t n, const pcr::DevView v,
+                                                         uint32_t* __restrict__ pix, unsigned long long* __restrict__ key) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint4 p = pts[i];
+    uint32_t px;
+    unsigned long long q;
+    const bool vis = pcr::project_fp64(v, __uint_as_float(p.x), __uint_as_float(p.y), __uint_as_float(p.z), &px, &q);
+    pix[i] = vis ? px : 0xFFFFFFFFu;
+    key[i] = vis ? pcr::make_key(q, p.w) : pcr::kEmptyKey;
+  }
+}
+
+// Pass 1 without the transform: one atomic minimum per visible fragment, in the order of the points (a warp
+// takes 32 consecutive points per step, as the passes do). Reads 12 B per point. With `filter`, each fragment
+// first reads the stored key (from L2) and skips the atomic unless its key is smaller: the stored key only
+// decreases, so a skipped key could never have become the minimum.
+__global__ void __launch_bounds__(256) k_pattern_min(const uint32_t* __restrict__ pix,
+                                                     const unsigned long long* __restrict__ key, uint64_t n,
+                                                     unsigned long long* __restrict__ keys, int filter) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint32_t p = __ldcs(pix + i);
+    const unsigned long long k = __ldcs(key + i);
+    if (p != 0xFFFFFFFFu && (!filter || k < __ldcg(keys + p))) atomicMin(keys + p, k);
+  }
+}
+
+// Pass 2 without the transform: per visible fragment the stored key of its pixel, the band test, and for an
+// accepted fragment the two colour/count additions.
+__global__ void __launch_bounds__(256) k_pattern_hq(const uint32_t* __restrict__ pix,
+                                                    const unsigned long long* __restrict__ key, uint64_t n,
+                                                    const unsigned long long* __restrict__ keys,
+                                                    unsigned long long* __restrict__ accum, uint32_t eps_num,
+                                                    uint32_t eps_den, unsigned long long nq) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint32_t p = __ldcs(pix + i);
+    const unsigned long long k = __ldcs(key + i);
+    if (p == 0xFFFFFFFFu) continue;
+    if (pcr::in_band(k >> 24, keys[p] >> 24, nq, eps_num, eps_den)) {
+      atomicAdd(accum + 2 * (uint64_t)p, pcr::hq_rg((uint32_t)k));
+      atomicAdd(accum + 2 * (uint64_t)p + 1, pcr::hq_bc((uint32_t)k));
+    }
+  }
+}
+
 int sms() {
   int dev = 0, v = 1;
   cudaGetDevice(&dev);
@@ -61,5 +111,49 @@ extern "C" int pcr_ceiling_stream_read(const void* d_src, uint64_t n16, uint32_t
   if (!d_src || !d_sink || (reinterpret_cast<uintptr_t>(d_src) & 15u)) return (int)cudaErrorInvalidValue;
   if (n16 == 0) return 0;
   k_stream_read<<<sms() * 64, 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const uint4*>(d_src), n16, d_sink);
+  return (int)cudaGetLastError();
+}
+
+extern "C" int pcr_ceiling_pattern_project(const void* d_points, uint64_t n, const double* m12, double near_,
+                                           double far_, int32_t width, int32_t height, uint32_t* d_pix,
+                                           uint64_t* d_key, void* stream) {
+  if (!d_points || !m12 || !d_pix || !d_key || width < 1 || height < 1 || width > 16384 || height > 16384 ||
+      !(near_ > 0.0) || !(far_ > near_) || (reinterpret_cast<uintptr_t>(d_points) & 15u))
+    return (int)cudaErrorInvalidValue;
+  if (n == 0) return 0;
+  pcr::DevView v{};
+  for (int i = 0; i < 12; ++i) v.m[i] = m12[i];
+  v.near_ = near_;
+  v.far_ = far_;
+  v.scale = 1099511627776.0 / (far_ - near_);
+  v.fwidth = (float)width;
+  v.fheight = (float)height;
+  v.width = width;
+  v.height = height;
+  v.depth_mode = 0;
+  k_pattern_project<<<sms() * 8, 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const uint4*>(d_points), n, v,
+                                                                  d_pix, reinterpret_cast<unsigned long long*>(d_key));
+  return (int)cudaGetLastError();
+}
+
+extern "C" int pcr_ceiling_pattern_min(const uint32_t* d_pix, const uint64_t* d_key, uint64_t n, uint64_t* d_keys,
+                                       int32_t filter, void* stream) {
+  if (!d_pix || !d_key || !d_keys || (filter != 0 && filter != 1)) return (int)cudaErrorInvalidValue;
+  if (n == 0) return 0;
+  k_pattern_min<<<sms() * 8, 256, 0, (cudaStream_t)stream>>>(
+      d_pix, reinterpret_cast<const unsigned long long*>(d_key), n, reinterpret_cast<unsigned long long*>(d_keys),
+      filter);
+  return (int)cudaGetLastError();
+}
+
+extern "C" int pcr_ceiling_pattern_hq(const uint32_t* d_pix, const uint64_t* d_key, uint64_t n, const uint64_t* d_keys,
+                                      uint64_t* d_accum, uint32_t eps_num, uint32_t eps_den, uint64_t nq,
+                                      void* stream) {
+  if (!d_pix || !d_key || !d_keys || !d_accum || eps_den == 0) return (int)cudaErrorInvalidValue;
+  if (n == 0) return 0;
+  k_pattern_hq<<<sms() * 8, 256, 0, (cudaStream_t)stream>>>(
+      d_pix, reinterpret_cast<const unsigned long long*>(d_key), n,
+      reinterpret_cast<const unsigned long long*>(d_keys), reinterpret_cast<unsigned long long*>(d_accum), eps_num,
+      eps_den, nq);
   return (int)cudaGetLastError();
 }
