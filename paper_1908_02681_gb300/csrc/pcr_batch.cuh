@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(kCertThreads, PCR_BATCH_MIN_BLOCKS) k_batch_pa
               defer = klo < keys[pix];
             }
           }
-          if (has) atomicMin(keys + pix, key);
+          if (has && key < stored_key(keys, pix)) atomicMin(keys + pix, key);
           unsigned dummy = 0;
           defer_points(defer, p, q, qn, lane, [&](const uint4& d) { raster_deferred(Pg, sF, d, keys, &dummy); });
         } else {

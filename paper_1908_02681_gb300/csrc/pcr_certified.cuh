@@ -586,8 +586,10 @@ __device__ __forceinline__ void load_table(const CertParams& P, const long long*
   __syncthreads();
 }
 
+// Pass 1 keeps two classified points per lane live across their stored-key reads: 64 registers, 4 blocks
+// per SM (at 40 or 48 registers it spills and runs 10-13 % slower).
 #ifndef PCR_CERT_MIN_BLOCKS
-#define PCR_CERT_MIN_BLOCKS 6
+#define PCR_CERT_MIN_BLOCKS 4
 #endif
 #ifndef PCR_CERT_THREADS
 #define PCR_CERT_THREADS 256
@@ -718,6 +720,14 @@ __device__ __noinline__ void raster_deferred(const CertParams& P, const long lon
   }
 }
 
+// The key a pixel holds, read from L2 (not L1). Pass 1 reads it before its atomic and skips the atomic when
+// the fragment's key is not below it: a stored key only decreases, so such a key can never become the
+// minimum, and the result is the same. On a coherent point order, where consecutive points share pixels, this
+// halves the atomic minima (same-address atomics serialise in L2).
+__device__ __forceinline__ unsigned long long stored_key(const unsigned long long* keys, uint32_t pix) {
+  return __ldcg(keys + pix);
+}
+
 // Commits one key per lane (has = true) with one atomic minimum per distinct pixel of the warp: lanes
 // whose fragments land on the same pixel are grouped (match.any) and their smallest key found with two
 // 32-bit warp reductions (high word, then low word among the lanes holding the smallest high word).
@@ -776,10 +786,12 @@ __global__ void __launch_bounds__(kCertThreads, PCR_CERT_MIN_BLOCKS) k_raster_ce
   uint4* q = queue[warp];
   uint32_t qn = 0;
   unsigned c_exact = 0, c_amb = 0, c_fp64 = 0, c_defer = 0;
-  auto point = [&](const uint4& p, bool valid) {
+  // Tier 1 for one point: returns whether it has a decided fragment (pix, key) to commit; a point that tier
+  // 1 cannot decide is queued for tier 2 here.
+  auto classify = [&](const uint4& p, bool valid, uint32_t& pix, unsigned long long& key) -> bool {
     bool defer = false, has = false;
-    uint32_t pix = 0;
-    unsigned long long key = 0;
+    pix = 0;
+    key = 0;
     if (valid) {
       if (kApprox) {
         const CertFrag f = classify_df(P, p);
@@ -804,14 +816,21 @@ __global__ void __launch_bounds__(kCertThreads, PCR_CERT_MIN_BLOCKS) k_raster_ce
         }
       }
     }
-    commit_min<kMerge>(has, pix, key, keys, lane);
     if (!kApprox)
       defer_points(defer, p, q, qn, lane, [&](const uint4& d) { raster_deferred(P, sF, d, keys, &c_fp64); });
+    return has;
   };
+  // the two points of a tile are classified before either commits, so that their stored-key reads overlap
   const bool done = stream_tiles(pts, n, ring[warp], bars[warp], lane,
                                  [&](const uint4& p0, bool v0, const uint4& p1, bool v1) {
-                                   point(p0, v0);
-                                   point(p1, v1);
+                                   uint32_t pix0, pix1;
+                                   unsigned long long key0, key1;
+                                   const bool has0 = classify(p0, v0, pix0, key0);
+                                   const unsigned long long s0 = has0 ? stored_key(keys, pix0) : 0ull;
+                                   const bool has1 = classify(p1, v1, pix1, key1);
+                                   const unsigned long long s1 = has1 ? stored_key(keys, pix1) : 0ull;
+                                   commit_min<kMerge>(has0 && key0 < s0, pix0, key0, keys, lane);
+                                   commit_min<kMerge>(has1 && key1 < s1, pix1, key1, keys, lane);
                                  });
   if (!done && lane == 0) atomicOr(status, kStatusTimeout);
   if (!kApprox && lane < qn) raster_deferred(P, sF, q[lane], keys, &c_fp64);
