@@ -422,6 +422,7 @@ def run_ours(args, wl):
     kernel_name = {"raster_atomicmin": "k_raster", "hq_accumulate": "k_hq"}[dominant]
     achieved = n * BYTES_PER_POINT / (per_kernel[dominant] * 1e-3) / 1e9
     pass1_pts = n / (per_kernel["raster_atomicmin"] * 1e-3)
+    hbm_pts = hbm_peak * 1e9 / BYTES_PER_POINT
     hbm_ms = n * BYTES_PER_POINT / (hbm_peak * 1e9) * 1e3
     floor1 = max(hbm_ms, min(pattern["pattern_atomicmin_ms"], pattern["pattern_atomicmin_filtered_ms"]))
     floor2 = max(hbm_ms, pattern["pattern_hq_ms"])
@@ -449,7 +450,10 @@ def run_ours(args, wl):
             "random_u64_atomics_per_s": atomic_rate, "stream_read_gbs": read_gbs, **pattern,
             "atomicmin_floor_ms": floor1, "hq_accumulate_floor_ms": floor2,
             "atomicmin_frac_of_floor": floor1 / per_kernel["raster_atomicmin"],
-            "hq_accumulate_frac_of_floor": floor2 / per_kernel["hq_accumulate"]},
+            "hq_accumulate_frac_of_floor": floor2 / per_kernel["hq_accumulate"],
+            # pass 1 against min(HBM points/s, random-order atomic rate at one atomic per point): the roofline
+            # defined on uniform random atomics, kept beside the measured floor of this cloud's own order
+            "atomicmin_frac_of_random_order_roofline": pass1_pts / min(hbm_pts, atomic_rate)},
         "clocks": clocks.summary(),
         "gpu_launches": launches,
         "device_status": status,
