@@ -517,8 +517,13 @@ __device__ __forceinline__ FastFrag classify_fast(const PP& P, const long long* 
   if (in_range & depth_in & small_e & ax_ok & (exact | amb_ok)) {
     st = exact ? kExact : kAmbiguous;
   } else {
+    // The bound E holds at any size (rho enters linearly; nothing assumes it small) while the values stay
+    // finite and w - dw > 0 (depth_in). Ex + Ey < 1e30 keeps E finite and, as Ex >= 5.65u W |ndx|, fx and fy
+    // below ~1.5e36: so a point far outside the image is culled here even where E is large (a point just
+    // in front of the camera and far to the side), instead of going to tier 2.
+    const bool finite_e = __fadd_rn(Ex, Ey) < 1e30f;
     const bool ax_out = (fx < -Ex) | (fx >= __fadd_ru(P.v.fwidth, Ex)) | (fy < -Ey) | (fy >= __fadd_ru(P.v.fheight, Ey));
-    st = in_range & (depth_out | (depth_in & small_e & ax_out)) ? kCulled : kDefer;
+    st = in_range & (depth_out | (depth_in & finite_e & ax_out)) ? kCulled : kDefer;
   }
   out.state = st;
   out.pixel = ky * (uint32_t)P.v.width + kx;
@@ -586,10 +591,14 @@ __device__ __forceinline__ void load_table(const CertParams& P, const long long*
   __syncthreads();
 }
 
-// Pass 1 keeps two classified points per lane live across their stored-key reads: 64 registers, 4 blocks
-// per SM (at 40 or 48 registers it spills and runs 10-13 % slower).
+// Pass 1 at 64 registers and 4 blocks per SM: no spills, and the fastest measured shape (6 blocks at 40
+// registers spills and runs 9 % slower on a 100M-point frame).
 #ifndef PCR_CERT_MIN_BLOCKS
 #define PCR_CERT_MIN_BLOCKS 4
+#endif
+// The double-float mode (no table, no deferral queue) fits 40 registers without spills and runs fastest at 6.
+#ifndef PCR_CERT_APPROX_MIN_BLOCKS
+#define PCR_CERT_APPROX_MIN_BLOCKS 6
 #endif
 #ifndef PCR_CERT_THREADS
 #define PCR_CERT_THREADS 256
@@ -771,7 +780,7 @@ __device__ __forceinline__ void defer_points(bool defer, const uint4& p, uint4* 
 // queued per warp in shared memory and handled 32 at a time by tier 2 and the FP64 arbiter. The points
 // arrive through the warp's bulk-copy ring (stream_tiles).
 template <bool kApprox, bool kMerge, bool kStats>
-__global__ void __launch_bounds__(kCertThreads, PCR_CERT_MIN_BLOCKS) k_raster_cert(
+__global__ void __launch_bounds__(kCertThreads, kApprox ? PCR_CERT_APPROX_MIN_BLOCKS : PCR_CERT_MIN_BLOCKS) k_raster_cert(
     const uint4* __restrict__ pts, uint64_t n, const __grid_constant__ CertParams P,
     unsigned long long* __restrict__ keys, unsigned long long* __restrict__ stats, uint32_t* __restrict__ status,
     const long long* __restrict__ table) {
@@ -786,12 +795,13 @@ __global__ void __launch_bounds__(kCertThreads, PCR_CERT_MIN_BLOCKS) k_raster_ce
   uint4* q = queue[warp];
   uint32_t qn = 0;
   unsigned c_exact = 0, c_amb = 0, c_fp64 = 0, c_defer = 0;
-  // Tier 1 for one point: returns whether it has a decided fragment (pix, key) to commit; a point that tier
-  // 1 cannot decide is queued for tier 2 here.
-  auto classify = [&](const uint4& p, bool valid, uint32_t& pix, unsigned long long& key) -> bool {
+  // Per point: tier 1 (or the double-float evaluation), the atomic minimum of a decided fragment whose key
+  // is below the stored key, then the deferral of a point tier 1 could not decide. Committing before the
+  // deferral keeps the fragment out of the registers that live across the out-of-line tier-2 call.
+  auto point = [&](const uint4& p, bool valid) {
     bool defer = false, has = false;
-    pix = 0;
-    key = 0;
+    uint32_t pix = 0;
+    unsigned long long key = 0;
     if (valid) {
       if (kApprox) {
         const CertFrag f = classify_df(P, p);
@@ -816,21 +826,14 @@ __global__ void __launch_bounds__(kCertThreads, PCR_CERT_MIN_BLOCKS) k_raster_ce
         }
       }
     }
+    commit_min<kMerge>(has && key < stored_key(keys, pix), pix, key, keys, lane);
     if (!kApprox)
       defer_points(defer, p, q, qn, lane, [&](const uint4& d) { raster_deferred(P, sF, d, keys, &c_fp64); });
-    return has;
   };
-  // the two points of a tile are classified before either commits, so that their stored-key reads overlap
   const bool done = stream_tiles(pts, n, ring[warp], bars[warp], lane,
                                  [&](const uint4& p0, bool v0, const uint4& p1, bool v1) {
-                                   uint32_t pix0, pix1;
-                                   unsigned long long key0, key1;
-                                   const bool has0 = classify(p0, v0, pix0, key0);
-                                   const unsigned long long s0 = has0 ? stored_key(keys, pix0) : 0ull;
-                                   const bool has1 = classify(p1, v1, pix1, key1);
-                                   const unsigned long long s1 = has1 ? stored_key(keys, pix1) : 0ull;
-                                   commit_min<kMerge>(has0 && key0 < s0, pix0, key0, keys, lane);
-                                   commit_min<kMerge>(has1 && key1 < s1, pix1, key1, keys, lane);
+                                   point(p0, v0);
+                                   point(p1, v1);
                                  });
   if (!done && lane == 0) atomicOr(status, kStatusTimeout);
   if (!kApprox && lane < qn) raster_deferred(P, sF, q[lane], keys, &c_fp64);

@@ -260,6 +260,27 @@ def test_certified_classification_rates(gpu):
     assert fp64 < 0.002 * len(pts) and tier2 < 0.05 * len(pts)
 
 
+def test_points_around_the_camera(gpu):
+    """A cloud surrounding the eye: many points lie just in front of the camera plane and far to the side, where
+    the pixel error bound E is large. Tier 1 culls them when the estimate is outside the image by more than E
+    (E holds at any size while it is finite); the result stays bit-exact and few points reach tier 2."""
+    import torch
+    rng = np.random.default_rng(5)
+    n = 2_000_000
+    pts = np.zeros((n, 4), np.uint32)
+    pts[:, :3] = rng.uniform(-20.0, 20.0, size=(n, 3)).astype(np.float32).view(np.uint32)
+    pts[:, 3] = rng.integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32)
+    view = scenes.View.lookat((0.0, 0.0, 0.0), (1.0, 0.3, 0.1), (0.0, 0.0, 1.0), 60.0, 1920, 1080, 0.01, 100.0)
+    fb = gpu.pcr_create_framebuffer(view.width, view.height)
+    counts = torch.zeros(4, dtype=torch.int64, device="cuda")
+    gpu.pcr_render_atomicmin_stats(fb, _dev(pts), view, counts)
+    tier1, amb, fp64, tier2 = (int(c) for c in counts.cpu())
+    keys, _ = gpu.pcr_framebuffer_keys(fb)
+    assert np.array_equal(gpu.keys_to_numpy(keys), oracle.render_atomicmin(pts, view))
+    print(f"\naround the camera: tier-1 exact {tier1}, tier 2 {tier2}, FP64 arbiter {fp64} of {n}")
+    assert tier2 < 0.005 * n
+
+
 @pytest.mark.parametrize("merge,blocks", [(0, 8), (1, 8), (1, 1), (1, 3), (0, 32)])
 def test_tuning_does_not_change_results(gpu, merge, blocks):
     import torch
