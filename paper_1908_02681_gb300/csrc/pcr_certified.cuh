@@ -52,13 +52,15 @@ struct CertParams {
   float H[3][4], L[3][4];             // float splits of the rows clip x, clip y, w (H: nearest float, L: rest)
   float delta_c;                      // |float(clip) - fma-chain estimate| <= delta_c * T (per row)
   float d_k1, d_k2;                   // tier-1 bound of t: D = d_k1 * T_w + d_k2
+  float half_d;                       // RD(1/2 - d_k2 - 2^-22): tier 1 tests |frac - 1/2| < half_d - d_k1 T_w
+  float k1_c, k2_c;                   // tier-1 pixel bound factors 0.506 (1 + 1e-6), 0.506 delta_c (1 + 1e-6)
+  float hw, hwm, hh, hhm, wm, hm;     // W/2, W/2 - 1/2, H/2, H/2 - 1/2, W - 1/2, H - 1/2 (exact)
   float near_in, far_in;              // w - dw > near_in => w >= near; w + dw < far_in => w < far (FP64 w)
   float near_out, far_out;            // w + dw < near_out => w < near; w - dw > far_out => w >= far
   float xyz_max;                      // |x| + |y| + |z| below this: table entries usable, values finite
   float kappa;                        // double-float error bound factor (relative to T)
   float t_c1, t_c2;                   // tier-2 bound of t: t_c1 * T_t + t_c2
   float Af[3], Bf;                    // float approximations of A_j and B (for T_t)
-  float ex_a1, ex_a2, ey_a1, ey_a2;   // tier-1 pixel bound constants (tier 1 folds them per point)
   unsigned long long BL;              // tier 1: B * 2^40 = BH * 2^32 + BL, 0 <= BL < 2^32
   long long BH;
   uint32_t B0, B1, B2;                // B * 2^40 as a 96-bit two's-complement integer (low word first)
@@ -75,7 +77,7 @@ struct CertParams {
 // The first-tier constants of one view (a subset of CertParams with the same field names).
 struct HotParams {
   float H[3][4];
-  float delta_c, d_k1, d_k2, near_in, far_in, near_out, far_out, xyz_max;
+  float delta_c, d_k1, half_d, k1_c, k2_c, hw, hwm, hh, hhm, wm, hm, near_in, far_in, near_out, far_out, xyz_max;
   unsigned long long BL;
   long long BH;
   struct {
@@ -90,7 +92,15 @@ __host__ __device__ inline HotParams hot_params(const CertParams& P) {
     for (int c = 0; c < 4; ++c) h.H[r][c] = P.H[r][c];
   h.delta_c = P.delta_c;
   h.d_k1 = P.d_k1;
-  h.d_k2 = P.d_k2;
+  h.half_d = P.half_d;
+  h.k1_c = P.k1_c;
+  h.k2_c = P.k2_c;
+  h.hw = P.hw;
+  h.hwm = P.hwm;
+  h.hh = P.hh;
+  h.hhm = P.hhm;
+  h.wm = P.wm;
+  h.hm = P.hm;
   h.near_in = P.near_in;
   h.far_in = P.far_in;
   h.near_out = P.near_out;
@@ -213,11 +223,24 @@ inline bool prepare_cert(const DevView& v, bool approximate, CertParams* P) {
   P->d_k2 = (float)(5.2 * u64 * (P->linear ? S * v.near_ : 0.0) + (double)P->t_c2);
   // |RN32(clip_FP64) - fma-chain estimate| <= (u + 4u + 3 u64) T_H, T_H <= (1 + 3u) T_computed
   P->delta_c = (float)(5.1 * uf);
-  // fx bound: W/2 (7u |ndc| + 1.01 rho)(1 + 5u) + 4.2u |fx| (see classify_fast)
-  P->ex_a1 = (float)(3.52 * uf * v.fwidth);
-  P->ex_a2 = (float)(0.506 * v.fwidth);
-  P->ey_a1 = (float)(3.52 * uf * v.fheight);
-  P->ey_a2 = (float)(0.506 * v.fheight);
+  // 1/2 - d_k2 - 2^-22, rounded down (the 2^-22 covers the 23-bit truncation of the fraction and the rounding
+  // of the fma that subtracts d_k1 T_w; see classify_fast)
+  {
+    const double hd = 0.5 - (double)P->d_k2 - 0x1p-22;
+    float f = (float)hd;
+    if ((double)f > hd) f = std::nextafter(f, -1.0f);
+    P->half_d = f;
+  }
+  // fx bound factors (see classify_fast): 0.506 and 0.506 delta_c, times 1 + 1e-6 for the approximate
+  // reciprocal of w - dw, rounded up
+  P->k1_c = std::nextafter((float)(0.506 * (1.0 + 1e-6)), 1.0f);
+  P->k2_c = std::nextafter((float)(0.506 * (double)P->delta_c * (1.0 + 1e-6)), 1.0f);
+  P->hw = 0.5f * v.fwidth;
+  P->hwm = 0.5f * v.fwidth - 0.5f;
+  P->hh = 0.5f * v.fheight;
+  P->hhm = 0.5f * v.fheight - 0.5f;
+  P->wm = v.fwidth - 0.5f;
+  P->hm = v.fheight - 0.5f;
   // float clip-plane thresholds with (1 +- 4u) margins for the rounding of w -+ dw
   // near_in also keeps t >= 2.5 and far_in keeps t <= 2^40 - 2^25 for w between them, so the tier-1 code of a
   // point it certifies as visible needs no sign, zero or cap check (t = S (w - near) or S w)
@@ -395,26 +418,6 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return r;
 }
 
-// Tier-1 pixel axis. f: float estimate of the definition's pixel coordinate; E: bound on their
-// distance; size: W or H (<= 16384). Returns 0 = inside [0, size) at pixel *px, 1 = certainly outside,
-// 2 = undecided (every comparison is written so that NaN or infinity lands here).
-__device__ __forceinline__ uint32_t pixel_axis(float f, float E, float size, uint32_t* px) {
-  if (!(E < 0.25f)) return 2u;
-  if (!(f >= 0.0f)) return f < -E ? 1u : 2u;
-  if (!(f < __fadd_rn(size, 1.0f))) return f >= __fadd_rn(size, 1.0f) ? 1u : 2u;
-  // floor via the 1.5 * 2^23 shift: for -0.5 <= f - 0.5 < 2^22 the sum lies in [2^23, 2^24), where floats
-  // are the integers, so it rounds f - 0.5 to the nearest integer: floor(f) unless f is an integer (then
-  // f - 1 or f; either way fr below falls outside [E, 1 - E) and the axis is undecided)
-  const float g = __fadd_rn(__fsub_rn(f, 0.5f), 12582912.0f);
-  const float fl = __fsub_rn(g, 12582912.0f);
-  const float fr = __fsub_rn(f, fl);  // exact: fl is an integer within 1 of f, both below 2^15
-  if (!(fr >= E && fr < __fsub_rn(1.0f, E))) return 2u;
-  const uint32_t k = (uint32_t)(__float_as_int(g) - 0x4B400000);  // bits of 1.5 * 2^23: g - 1.5 * 2^23
-  if (fl >= size) return 1u;
-  *px = k;
-  return 0u;
-}
-
 // Tier-1 result: state, pixel, and the fixed-point t as three 32-bit words (t * 2^40, low word first).
 struct FastFrag {
   uint32_t state;  // kCulled, kExact, kAmbiguous (code qc - 1 or qc when lo_half, else qc or qc + 1), kDefer
@@ -449,8 +452,7 @@ __device__ __forceinline__ FastFrag classify_fast(const PP& P, const long long* 
   const bool in_range = __fadd_rn(__fadd_rn(fabsf(x), fabsf(y)), fabsf(z)) < P.xyz_max;
   // float estimates of w and its term magnitude (fma chains, as the FP64 definition orders them)
   const float w = __fmaf_rn(P.H[2][2], z, __fmaf_rn(P.H[2][1], y, __fmaf_rn(P.H[2][0], x, P.H[2][3])));
-  const float Tw = __fmaf_rn(fabsf(P.H[2][2]), fabsf(z),
-                             __fmaf_rn(fabsf(P.H[2][1]), fabsf(y), __fmaf_rn(fabsf(P.H[2][0]), fabsf(x), fabsf(P.H[2][3]))));
+  const float Tw = __fmaf_rn(fabsf(P.H[2][2]), fabsf(z), __fmaf_rn(fabsf(P.H[2][1]), fabsf(y), __fmaf_rn(fabsf(P.H[2][0]), fabsf(x), fabsf(P.H[2][3]))));
   const float dw = __fmul_rn(P.delta_c, Tw);
   const float wlo = __fsub_rd(w, dw), whi = __fadd_ru(w, dw);  // directed: wlo <= w - dw, whi >= w + dw
   // predicates combined with bitwise & and |: every operand is computed anyway, and this keeps the
@@ -476,53 +478,64 @@ __device__ __forceinline__ FastFrag classify_fast(const PP& P, const long long* 
       : "r"((uint32_t)(L >> 32)), "r"((uint32_t)Hh), "r"((uint32_t)((unsigned long long)Hh >> 32)));
   const float frac =
       __fsub_rn(__uint_as_float(0x3F800000u | (__funnelshift_r(out.a0, out.a1, 17) & 0x7FFFFFu)), 1.0f);
-  const float D = __fadd_rn(__fmaf_rn(P.d_k1, Tw, P.d_k2), 0x1p-22f);
-  // D < frac < 1 - D as |frac - 1/2| < 1/2 - D (frac - 1/2 is exact; the rounding of 1/2 - D is far inside
-  // the 2^-22 slack of D). An undecided code still has two usable candidates while D < 1/4.
-  const bool exact = fabsf(__fsub_rn(frac, 0.5f)) < __fsub_rn(0.5f, D);
+  // The code is floor(t_FP64) when D < frac_exact < 1 - D, D = d_k1 T_w + d_k2 (the FP64 rounding and the
+  // fixed-point sum's error). frac is the fraction truncated to 23 bits (frac <= frac_exact < frac + 2^-23).
+  // hD = RN(half_d - d_k1 T_w), half_d = RD(1/2 - d_k2 - 2^-22), is within 2^-25 of its real value, so
+  // |frac - 1/2| < hD (frac - 1/2 is exact) gives D + 2^-22 - 2^-25 < frac and frac + 2^-23 < 1 - D.
+  // hD > 1/4 gives D < 1/4: an undecided code still has two usable candidates.
+  const float hD = __fmaf_rn(-P.d_k1, Tw, P.half_d);
+  const bool exact = fabsf(__fsub_rn(frac, 0.5f)) < hD;
   out.lo_half = frac < 0.5f;
-  const bool amb_ok = D < 0.25f;
+  const bool amb_ok = hD > 0.25f;
   // ---- pixel estimate
   const float cx = __fmaf_rn(P.H[0][2], z, __fmaf_rn(P.H[0][1], y, __fmaf_rn(P.H[0][0], x, P.H[0][3])));
-  const float Tx = __fmaf_rn(fabsf(P.H[0][2]), fabsf(z),
-                             __fmaf_rn(fabsf(P.H[0][1]), fabsf(y), __fmaf_rn(fabsf(P.H[0][0]), fabsf(x), fabsf(P.H[0][3]))));
+  const float Tx = __fmaf_rn(fabsf(P.H[0][2]), fabsf(z), __fmaf_rn(fabsf(P.H[0][1]), fabsf(y), __fmaf_rn(fabsf(P.H[0][0]), fabsf(x), fabsf(P.H[0][3]))));
   const float cy = __fmaf_rn(P.H[1][2], z, __fmaf_rn(P.H[1][1], y, __fmaf_rn(P.H[1][0], x, P.H[1][3])));
-  const float Ty = __fmaf_rn(fabsf(P.H[1][2]), fabsf(z),
-                             __fmaf_rn(fabsf(P.H[1][1]), fabsf(y), __fmaf_rn(fabsf(P.H[1][0]), fabsf(x), fabsf(P.H[1][3]))));
-  // with wlo > near_in > 0: rcp.approx (relative error <= 2^-23); (1 + 1e-6) makes rden >= 1 / (w - dw)
+  const float Ty = __fmaf_rn(fabsf(P.H[1][2]), fabsf(z), __fmaf_rn(fabsf(P.H[1][1]), fabsf(y), __fmaf_rn(fabsf(P.H[1][0]), fabsf(x), fabsf(P.H[1][3]))));
+  // with wlo > near_in > 0: rcp.approx (relative error <= 2^-23); r0 (1 + 1e-6) >= 1 / (w - dw), and the
+  // factor 1 + 1e-6 is folded into k1_c and k2_c
   const float rw = rcp_approx(w);
-  const float rden = __fmul_rn(rcp_approx(wlo), 1.000001f);
+  const float r0 = rcp_approx(wlo);
   const float ndx = __fmul_rn(cx, rw), ndy = __fmul_rn(cy, rw);
-  const float fx = __fmul_rn(__fmaf_rn(ndx, 0.5f, 0.5f), P.v.fwidth);
-  const float fy = __fmul_rn(__fmaf_rn(ndy, 0.5f, 0.5f), P.v.fheight);
+  // fm = fx - 1/2 for the pixel coordinate fx = (nd / 2 + 1/2) W, in one rounding: fm = RN(nd W/2 + (W/2 - 1/2))
+  const float fxm = __fmaf_rn(ndx, P.hw, P.hwm), fym = __fmaf_rn(ndy, P.hh, P.hhm);
   // |fx_FP64 - fx| <= E = W ((3.52u + 0.506 rho') |nd| + 0.506 rden dc T + 2.13u (|nd| + 1)) + 2^-20 with
-  // rho' = rden dw (see the file header); |fx| <= W (|nd| + 1) / 2 folds the 4.25u |fx| term
-  const float k1 = __fmaf_rn(0.506f, __fmul_rn(rden, dw), 5.65f * 0x1p-24f);
-  const float k2 = __fmul_rn(__fmul_rn(0.506f, rden), P.delta_c);
-  const float Ex = __fmaf_rn(P.v.fwidth, __fmaf_rn(k1, fabsf(ndx), __fmaf_rn(k2, Tx, 2.13f * 0x1p-24f)), 0x1p-20f);
-  const float Ey = __fmaf_rn(P.v.fheight, __fmaf_rn(k1, fabsf(ndy), __fmaf_rn(k2, Ty, 2.13f * 0x1p-24f)), 0x1p-20f);
-  // floor via the 1.5 * 2^23 shift: for -0.5 <= f - 0.5 < 2^22 the sum lies in [2^23, 2^24), where floats
-  // are the integers, so it rounds f - 0.5 to the nearest integer: floor(f) unless f is an integer (then
-  // f - 1 or f, and fr below falls outside [E, 1 - E)). Outside that range k is far above the image size.
-  const float gx = __fadd_rn(__fsub_rn(fx, 0.5f), 12582912.0f), gy = __fadd_rn(__fsub_rn(fy, 0.5f), 12582912.0f);
+  // rho' = rden dw (see the file header); |fx| <= W (|nd| + 1) / 2 folds the 4.25u |fx| term, and one
+  // rounding of fm (instead of two for fx) stays inside it. Tier 1 uses hE = RN(1/2 - 2^-19 - (E - 2^-20)),
+  // within 2^-25 of its real value, so hE < 1/2 - E - 2^-20 + 2^-25.
+  const float k1 = __fmaf_rn(P.k1_c, __fmul_rn(r0, dw), 5.65f * 0x1p-24f);
+  const float k2 = __fmul_rn(r0, P.k2_c);
+  const float hEx = __fmaf_rn(-P.v.fwidth, __fmaf_rn(k1, fabsf(ndx), __fmaf_rn(k2, Tx, 2.13f * 0x1p-24f)),
+                              0.5f - 0x1p-19f);
+  const float hEy = __fmaf_rn(-P.v.fheight, __fmaf_rn(k1, fabsf(ndy), __fmaf_rn(k2, Ty, 2.13f * 0x1p-24f)),
+                              0.5f - 0x1p-19f);
+  // floor of fx = fm + 1/2 via the 1.5 * 2^23 shift: for -1/2 <= fm < 2^22 the sum lies in [2^23, 2^24), where
+  // floats are the integers, so g rounds fm to the nearest integer k: floor(fx) unless fx is an integer (then
+  // fx - 1 or fx, and |fm - k| = 1/2 fails the test below). Outside that range k, read from the bits, is
+  // negative or above 2^22 as an unsigned number: never below the image size.
+  const float gx = __fadd_rn(fxm, 12582912.0f), gy = __fadd_rn(fym, 12582912.0f);
   const uint32_t kx = (uint32_t)(__float_as_int(gx) - 0x4B400000), ky = (uint32_t)(__float_as_int(gy) - 0x4B400000);
-  const float frx = __fsub_rn(fx, __fsub_rn(gx, 12582912.0f)), fry = __fsub_rn(fy, __fsub_rn(gy, 12582912.0f));
-  const bool small_e = __fadd_rn(Ex, Ey) < 0.25f;
-  // E < fr < 1 - E, as |fr - 1/2| < 1/2 - E: the subtraction fr - 1/2 is exact (fr in [-1, 2]), and
-  // rounding 1/2 - E (below 2^-20 from its value) is covered by the 2^-20 slack in E
-  const bool ax_ok = (kx < (uint32_t)P.v.width) & (ky < (uint32_t)P.v.height) &
-                     (fabsf(__fsub_rn(frx, 0.5f)) < __fsub_rn(0.5f, Ex)) & (fabsf(__fsub_rn(fry, 0.5f)) < __fsub_rn(0.5f, Ey));
+  // fm - k = fr - 1/2 (fr = fx - k), exact (k is an integer within 1/2 of fm, both below 2^22)
+  const float dx = __fsub_rn(fxm, __fsub_rn(gx, 12582912.0f)), dy = __fsub_rn(fym, __fsub_rn(gy, 12582912.0f));
+  // E + E' < 1/4, as hE + hE' > 3/4 (conservative by the extra 2^-20 in each hE)
+  const bool small_e = __fadd_rn(hEx, hEy) > 0.75f;
+  // E < fr < 1 - E for both axes: |fm - k| < hE < 1/2 - E
+  const bool ax_ok = (kx < (uint32_t)P.v.width) & (ky < (uint32_t)P.v.height) & (fabsf(dx) < hEx) & (fabsf(dy) < hEy);
   // ---- state (the visible case first; the cull tests only where it fails)
   uint32_t st;
   if (in_range & depth_in & small_e & ax_ok & (exact | amb_ok)) {
     st = exact ? kExact : kAmbiguous;
   } else {
+    // Upper bounds of E: 1/2 - hE, rounded up (>= E + 2^-20 - 2^-25).
+    const float Ex = __fadd_ru(0.5f, -hEx), Ey = __fadd_ru(0.5f, -hEy);
     // The bound E holds at any size (rho enters linearly; nothing assumes it small) while the values stay
     // finite and w - dw > 0 (depth_in). Ex + Ey < 1e30 keeps E finite and, as Ex >= 5.65u W |ndx|, fx and fy
     // below ~1.5e36: so a point far outside the image is culled here even where E is large (a point just
     // in front of the camera and far to the side), instead of going to tier 2.
     const bool finite_e = __fadd_rn(Ex, Ey) < 1e30f;
-    const bool ax_out = (fx < -Ex) | (fx >= __fadd_ru(P.v.fwidth, Ex)) | (fy < -Ey) | (fy >= __fadd_ru(P.v.fheight, Ey));
+    // fx_FP64 < 0 when fm + 1/2 + E < 0; fx_FP64 >= W when fm + 1/2 - E >= W (directed roundings)
+    const bool ax_out = (fxm < -__fadd_ru(0.5f, Ex)) | (fxm >= __fadd_ru(P.wm, Ex)) | (fym < -__fadd_ru(0.5f, Ey)) |
+                        (fym >= __fadd_ru(P.hm, Ey));
     st = in_range & (depth_out | (depth_in & finite_e & ax_out)) ? kCulled : kDefer;
   }
   out.state = st;
@@ -906,11 +919,11 @@ __device__ __noinline__ void hq_deferred(const CertParams& P, const long long* s
   if (accept) hq_add(accum, pix, p.w);
 }
 
-// Pass 2 (Section 2.2) with the certified transform, same two tiers and the same point staging as pass 1.
-// Pass 2 keeps two classified points per lane live across the stored-key reads: 64 registers, 4 blocks
-// per SM (at 40 registers it spills).
+// Pass 2 (Section 2.2) with the certified transform, same two tiers and the same point staging as pass 1,
+// one point at a time at 48 registers and 5 blocks per SM (the fastest measured shape: two points per lane
+// with both stored-key reads in flight needs 64 registers and 4 blocks, and ran 1-2 % slower).
 #ifndef PCR_HQ_MIN_BLOCKS
-#define PCR_HQ_MIN_BLOCKS 4
+#define PCR_HQ_MIN_BLOCKS 5
 #endif
 template <bool kApprox, bool kMerge>
 __global__ void __launch_bounds__(kCertThreads, PCR_HQ_MIN_BLOCKS) k_hq_cert(
@@ -927,59 +940,45 @@ __global__ void __launch_bounds__(kCertThreads, PCR_HQ_MIN_BLOCKS) k_hq_cert(
   if (!kApprox) load_table(P, table, sF);
   uint4* q = queue[warp];
   uint32_t qn = 0;
-  // the two points of a tile are classified together so that their stored-key reads overlap
-  const bool done = stream_tiles(pts, n, ring[warp], bars[warp], lane,
-                                 [&](const uint4& p0, bool v0, const uint4& p1, bool v1) {
-    const uint4 pp[2] = {p0, p1};
-    const bool vv[2] = {v0, v1};
-    bool defer[2], accept[2];
-    uint32_t pix[2];
-    if (kApprox) {
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        defer[u] = accept[u] = false;
-        pix[u] = 0;
-        if (vv[u]) {
-          const CertFrag f = classify_df(P, pp[u]);
-          pix[u] = f.pixel;
-          defer[u] = hq_decide(P, f, keys, eps_num, eps_den, &accept[u]);
-        }
-      }
-    } else {
-      FastFrag f[2];
-      unsigned long long stored[2];
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        f[u] = classify_fast(P, sF, pp[u]);
-        pix[u] = f[u].pixel;
-        const bool coded = vv[u] & ((f[u].state == kExact) | (f[u].state == kAmbiguous));
-        stored[u] = coded ? stored_key(keys, pix[u]) : 0ull;
-      }
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        defer[u] = vv[u] & (f[u].state == kDefer);
-        accept[u] = false;
-        if (vv[u] & ((f[u].state == kExact) | (f[u].state == kAmbiguous))) {
-          const unsigned long long qmin = stored[u] >> 24;
-          const unsigned long long qc = code_from_fixed(f[u].a1, f[u].a2);
-          const bool amb = f[u].state == kAmbiguous;
-          accept[u] = in_band(amb && f[u].lo_half ? qc - 1 : qc, qmin, P.v.nq, eps_num, eps_den);
+  // Per point: tier 1 (or the double-float evaluation), the band test against the stored key, the colour
+  // and count additions of an accepted fragment, then the deferral of a point tier 1 could not decide.
+  auto point = [&](const uint4& p, bool valid) {
+    bool defer = false, accept = false;
+    uint32_t pix = 0;
+    if (valid) {
+      if (kApprox) {
+        const CertFrag f = classify_df(P, p);
+        pix = f.pixel;
+        defer = hq_decide(P, f, keys, eps_num, eps_den, &accept);
+      } else {
+        const FastFrag f = classify_fast(P, sF, p);
+        pix = f.pixel;
+        defer = f.state == kDefer;
+        if ((f.state == kExact) | (f.state == kAmbiguous)) {
+          const unsigned long long qmin = stored_key(keys, pix) >> 24;
+          const unsigned long long qc = code_from_fixed(f.a1, f.a2);
+          const bool amb = f.state == kAmbiguous;
+          // an undecided code (candidates qc - 1, qc or qc, qc + 1) is settled here when both candidates
+          // give the same band answer, else the point goes to tier 2
+          accept = in_band(amb && f.lo_half ? qc - 1 : qc, qmin, P.v.nq, eps_num, eps_den);
           if (amb) {
-            const bool other = in_band(f[u].lo_half ? qc : qc + 1, qmin, P.v.nq, eps_num, eps_den);
-            defer[u] = accept[u] != other;
-            accept[u] = accept[u] && !defer[u];
+            const bool other = in_band(f.lo_half ? qc : qc + 1, qmin, P.v.nq, eps_num, eps_den);
+            defer = accept != other;
+            accept = accept && !defer;
           }
         }
       }
     }
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      commit_add<kMerge>(accept[u], pix[u], pp[u].w, accum, lane);
-      if (!kApprox)
-        defer_points(defer[u], pp[u], q, qn, lane,
-                     [&](const uint4& d) { hq_deferred(P, sF, d, keys, accum, eps_num, eps_den); });
-    }
-  });
+    commit_add<kMerge>(accept, pix, p.w, accum, lane);
+    if (!kApprox)
+      defer_points(defer, p, q, qn, lane,
+                   [&](const uint4& d) { hq_deferred(P, sF, d, keys, accum, eps_num, eps_den); });
+  };
+  const bool done = stream_tiles(pts, n, ring[warp], bars[warp], lane,
+                                 [&](const uint4& p0, bool v0, const uint4& p1, bool v1) {
+                                   point(p0, v0);
+                                   point(p1, v1);
+                                 });
   if (!done && lane == 0) atomicOr(status, kStatusTimeout);
   if (!kApprox && lane < qn) hq_deferred(P, sF, q[lane], keys, accum, eps_num, eps_den);
 }
