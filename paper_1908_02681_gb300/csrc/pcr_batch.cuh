@@ -184,6 +184,11 @@ __global__ void __launch_bounds__(kCertThreads, PCR_BATCH_MIN_BLOCKS) k_batch_pa
     const BatchSlot& S = slots[v];
     unsigned long long* const keys = S.keys;
     unsigned long long* const accum = S.accum;
+    // the framebuffer pointers come from device memory, so the compiler cannot infer their address space;
+    // stated here, the atomics compile to fire-and-forget global reductions instead of generic atomics that
+    // return the old value
+    __builtin_assume(__isGlobal(keys));
+    __builtin_assume(accum == nullptr || __isGlobal(accum));
     uint32_t qn = 0;
     // the item's points as one sequence of steps (kChunk / kCertThreads per chunk); the point of the next
     // step is loaded before the current one is classified, so its memory latency overlaps the work
