@@ -94,8 +94,10 @@ typedef struct {
 /* Launch tuning of a framebuffer's point passes (the knobs an autotuner sets). Results never depend on it. */
 typedef struct {
   int32_t merge_same_pixel; /* 1: the fragments of one warp that land on the same pixel are merged with warp
-                               reductions, then one atomic per pixel; 0 (default): one atomic per fragment */
-  int32_t blocks_per_sm;    /* 256-thread blocks per SM for the point passes, 1..32 (default 8) */
+                               reductions, then one atomic per pixel; 0 (default): one atomic per fragment
+                               (in pass 1 only where the fragment's key is below the key the pixel holds) */
+  int32_t blocks_per_sm;    /* 256-thread blocks per SM for the point passes, 1..32 (default 8; capped at the
+                               blocks that can be resident, 4 for pass 1 and 5 for pass 2) */
 } pcr_tuning;
 
 /* Framebuffer flags. */
@@ -132,7 +134,8 @@ pcr_status pcr_framebuffer_info(const pcr_framebuffer* fb, int32_t* width, int32
 pcr_status pcr_clear(pcr_framebuffer* fb, pcr_stream_t stream);
 
 /* Section 2.1: rasterizes n points into fb with one 64-bit atomic minimum per visible fragment (keys
- * accumulate with what fb holds; call pcr_clear or resolve with clear_after to start a frame).
+ * accumulate with what fb holds; call pcr_clear or resolve with clear_after to start a frame). A fragment
+ * whose key is not below the key its pixel already holds skips its atomic: the result is the same.
  * n == 0 is a no-op; n < 2^40. */
 pcr_status pcr_render_atomicmin(pcr_framebuffer* fb, const pcr_point* d_points, uint64_t n, const pcr_view* view,
                                 pcr_stream_t stream);
