@@ -150,6 +150,18 @@ pcr_status pcr_render_atomicmin(pcr_framebuffer* fb, const pcr_point* d_points, 
 pcr_status pcr_render_atomicmin_stats(pcr_framebuffer* fb, const pcr_point* d_points, uint64_t n,
                                       const pcr_view* view, uint64_t* d_counts, pcr_stream_t stream);
 
+/* Sections 1 and 2.1, per point and without a framebuffer: the fragment each of the n points gets under the
+ * view at width x height. d_pixel[i] = row * width + column (row 0 = bottom) of point i, or 0xFFFFFFFF when
+ * the definition culls it; d_key[i] = its key (depth code << 24 | RGB), or 0xFFFFFFFFFFFFFFFF when culled.
+ * The view's transform applies: EXACT and FP64 give the FP64 definition bit for bit, DOUBLE_FLOAT its
+ * approximation. The framebuffer passes take the same per-point decisions; a framebuffer keeps, per pixel,
+ * the smallest key that lands there.
+ * d_points: 16-byte aligned device memory, caller-owned; d_pixel (n u32) and d_key (n u64): caller-owned
+ * device memory. Asynchronous on stream; argument errors are synchronous and enqueue nothing; n == 0 is a
+ * no-op; n < 2^40; width, height in 1..16384. */
+pcr_status pcr_project_points(const pcr_point* d_points, uint64_t n, const pcr_view* view, int32_t width,
+                              int32_t height, uint32_t* d_pixel, uint64_t* d_key, pcr_stream_t stream);
+
 /* Section 2.2: high-quality splatting of n points into an HQ framebuffer: pass 1 = pcr_render_atomicmin;
  * pass 2 adds (R, G, B, 1) of every fragment with eps_den * (q - qmin) <= eps_num * (qmin + Nq) to its
  * pixel's sums, where qmin = key >> 24 after pass 1 and Nq = floor(near * s) (LINEAR) or 0 (METRIC), i.e.

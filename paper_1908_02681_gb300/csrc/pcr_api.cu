@@ -13,6 +13,7 @@
 #include "pcr_batch.cuh"
 #include "pcr_certified.cuh"
 #include "pcr_kernels.cuh"
+#include "pcr_project.cuh"
 
 struct pcr_framebuffer {
   int32_t width, height;
@@ -372,6 +373,32 @@ pcr_status pcr_render_atomicmin(pcr_framebuffer* fb, const pcr_point* d_points, 
   if (pcr_status st = make_dev_view(view, fb->width, fb->height, &dv)) return st;
   if (n == 0) return PCR_OK;
   return launch_raster(fb, d_points, n, dv, view->transform, (cudaStream_t)stream);
+}
+
+pcr_status pcr_project_points(const pcr_point* d_points, uint64_t n, const pcr_view* view, int32_t width,
+                              int32_t height, uint32_t* d_pixel, uint64_t* d_key, pcr_stream_t stream) {
+  if (pcr_status st = check_points(d_points, n)) return st;
+  if (width < 1 || width > 16384 || height < 1 || height > 16384)
+    return fail(PCR_ERR_INVALID_ARG, "width and height must be in 1..16384 (got %d x %d)", width, height);
+  if (n > 0 && (!d_pixel || !d_key)) return fail(PCR_ERR_INVALID_ARG, "d_pixel and d_key must not be NULL");
+  pcr::DevView dv;
+  if (pcr_status st = make_dev_view(view, width, height, &dv)) return st;
+  if (n == 0) return PCR_OK;
+  int device = 0;
+  if (const cudaError_t e = cudaGetDevice(&device)) return cuda_fail(e, "cudaGetDevice");
+  const cudaStream_t s = (cudaStream_t)stream;
+  const uint4* pts = reinterpret_cast<const uint4*>(d_points);
+  unsigned long long* keys = reinterpret_cast<unsigned long long*>(d_key);
+  const unsigned grid = grid_for(n, 256, device, 8);
+  const pcr::CertParams* P = nullptr;
+  const bool approx = view->transform == PCR_TRANSFORM_DOUBLE_FLOAT;
+  if (view->transform == PCR_TRANSFORM_FP64 || !pcr::cached_cert(dv, approx, &P))
+    pcr::k_project_fp64<<<grid, 256, 0, s>>>(pts, n, dv, d_pixel, keys);
+  else if (approx)
+    pcr::k_project_cert<true><<<grid, 256, 0, s>>>(pts, n, *P, d_pixel, keys);
+  else
+    pcr::k_project_cert<false><<<grid, 256, 0, s>>>(pts, n, *P, d_pixel, keys);
+  return after_launch("k_project");
 }
 
 pcr_status pcr_render_atomicmin_stats(pcr_framebuffer* fb, const pcr_point* d_points, uint64_t n,

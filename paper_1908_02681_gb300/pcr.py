@@ -74,6 +74,8 @@ def _declare(lib):
         "pcr_clear": ([_P, _P], S),
         "pcr_render_atomicmin": ([_P, _P, ctypes.c_uint64, ctypes.POINTER(pcr_view), _P], S),
         "pcr_render_atomicmin_stats": ([_P, _P, ctypes.c_uint64, ctypes.POINTER(pcr_view), _P, _P], S),
+        "pcr_project_points": ([_P, ctypes.c_uint64, ctypes.POINTER(pcr_view), ctypes.c_int32, ctypes.c_int32, _P, _P,
+                                _P], S),
         "pcr_render_hq_splat": ([_P, _P, ctypes.c_uint64, ctypes.POINTER(pcr_view), ctypes.c_uint32, ctypes.c_uint32,
                                  _P], S),
         "pcr_hq_accumulate": ([_P, _P, ctypes.c_uint64, ctypes.POINTER(pcr_view), ctypes.c_uint32, ctypes.c_uint32,
@@ -261,6 +263,27 @@ def pcr_render_atomicmin_stats(fb: Framebuffer, points, view, counts, stream=Non
         raise ValueError("counts must be a CUDA tensor of at least 4 8-byte words")
     _check(load().pcr_render_atomicmin_stats(fb.handle, ptr, n, ctypes.byref(v), ctypes.c_void_p(counts.data_ptr()),
                                              _stream(stream)))
+
+
+def pcr_project_points(points, view, pixel=None, key=None, stream=None):
+    """Per point, the fragment the view gives it: (pixel, key) as CUDA tensors, int32[n] (row * width +
+    column, -1 when culled) and int64[n] (bit patterns of the u64 keys, -1 when culled). The view's width and
+    height set the image. pixel and key may be given (CUDA, contiguous, n elements of 4 and 8 bytes)."""
+    import torch
+    ptr, n = _points_ptr(points)
+    v = make_view(view)
+    dev = points.device
+    if pixel is None:
+        pixel = torch.empty(n, dtype=torch.int32, device=dev)
+    if key is None:
+        key = torch.empty(n, dtype=torch.int64, device=dev)
+    for t, size in ((pixel, 4), (key, 8)):
+        if not t.is_cuda or t.element_size() != size or not t.is_contiguous() or t.numel() != n:
+            raise ValueError("pixel and key must be contiguous CUDA tensors of n 4-byte and n 8-byte words")
+    _check(load().pcr_project_points(ptr, n, ctypes.byref(v), int(view.width), int(view.height),
+                                     ctypes.c_void_p(pixel.data_ptr()), ctypes.c_void_p(key.data_ptr()),
+                                     _stream(stream)))
+    return pixel, key
 
 
 def pcr_render_hq_splat(fb: Framebuffer, points, view, eps_num: int = 1, eps_den: int = 100, stream=None):

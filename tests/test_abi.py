@@ -60,6 +60,19 @@ def test_host_argument_checks(lib):
     assert lib.pcr_resolve(None, None, 0, 0, None) == pcr.PCR_ERR_INVALID_ARG
     assert lib.pcr_get_device_status(None, None) == pcr.PCR_ERR_INVALID_ARG
     assert lib.pcr_destroy_framebuffer(None) == pcr.PCR_OK
+    # pcr_project_points: every argument error is found on the host, before any device call
+    from tests.helpers import axis_view
+    good = pcr.make_view(axis_view())
+    assert lib.pcr_project_points(ctypes.c_void_p(8), 4, ctypes.byref(good), 16, 16, ctypes.c_void_p(16),
+                                  ctypes.c_void_p(16), None) == pcr.PCR_ERR_INVALID_ARG  # misaligned points
+    assert "aligned" in pcr.pcr_last_error_message()
+    assert lib.pcr_project_points(ctypes.c_void_p(16), 4, ctypes.byref(good), 0, 16, ctypes.c_void_p(16),
+                                  ctypes.c_void_p(16), None) == pcr.PCR_ERR_INVALID_ARG
+    assert lib.pcr_project_points(ctypes.c_void_p(16), 4, ctypes.byref(good), 16, 16, None,
+                                  ctypes.c_void_p(16), None) == pcr.PCR_ERR_INVALID_ARG
+    assert lib.pcr_project_points(ctypes.c_void_p(16), 4, None, 16, 16, ctypes.c_void_p(16),
+                                  ctypes.c_void_p(16), None) == pcr.PCR_ERR_INVALID_ARG
+    assert lib.pcr_project_points(None, 0, ctypes.byref(good), 16, 16, None, None, None) == pcr.PCR_OK
 
 
 def test_view_marshalling():
