@@ -7,7 +7,9 @@ the depth code (Section 1: depth precision is lost in the vertex transformation)
 
 * PCR_TRANSFORM_EXACT and PCR_TRANSFORM_FP64 must equal the FP64 oracle bit for bit.
 * PCR_TRANSFORM_DOUBLE_FLOAT (float pairs, no FP64 arbiter) is measured: share of covered pixels whose
-  40-bit depth code differs from the oracle's, and share whose resolved colour differs. The numbers are
+  40-bit depth code differs from the oracle's, and share whose resolved colour differs; per point, share of
+  the visible points whose fragment (pixel or 40-bit code) differs, whose pixel differs, and whose
+  visibility differs, against the EXACT transform's per-point fragments. The numbers are
   printed (run with -s) and appended to $PCR_PRECISION_OUT when that variable names a file.
 """
 from __future__ import annotations
@@ -41,14 +43,28 @@ def _study(gpu, name, pts, view):
     exact = _render(gpu, dev, view, 0)
     assert np.array_equal(exact, ref), np.count_nonzero(exact != ref)
     df = _render(gpu, dev, view, 2)
-    del dev
+    # per point: the double-float fragment against the EXACT one (which equals the definition point by point,
+    # tests/test_gpu_project.py), counted on the device
+    view.transform = 0
+    pe, ke = gpu.pcr_project_points(dev, view)
+    view.transform = 2
+    pd, kd = gpu.pcr_project_points(dev, view)
+    visible = pe != -1
+    n_vis = int(visible.sum().item())
+    pt_code = int(((visible & ((ke >> 24) != (kd >> 24))) | (visible & (pe != pd))).sum().item())
+    pt_pixel = int((visible & (pe != pd)).sum().item())
+    pt_culled = int((visible != (pd != -1)).sum().item())
+    del pe, ke, pd, kd, visible, dev
     covered = ref != oracle.EMPTY
     n_cov = int(np.count_nonzero(covered))
     code_diff = int(np.count_nonzero((df >> np.uint64(24)) != (ref >> np.uint64(24))))
     colour_diff = int(np.count_nonzero(oracle.resolve_basic(df) != oracle.resolve_basic(ref)))
     row = {"scene": name, "points": int(len(pts)), "width": view.width, "height": view.height,
            "covered_pixels": n_cov, "double_float_code_mismatch": code_diff / max(n_cov, 1),
-           "double_float_colour_mismatch": colour_diff / max(n_cov, 1), "exact_transform_bit_exact": True}
+           "double_float_colour_mismatch": colour_diff / max(n_cov, 1), "exact_transform_bit_exact": True,
+           "visible_points": n_vis, "double_float_point_fragment_mismatch": pt_code / max(n_vis, 1),
+           "double_float_point_pixel_mismatch": pt_pixel / max(n_vis, 1),
+           "double_float_point_cull_mismatch": pt_culled / max(n_vis, 1)}
     print("\nprecision:", json.dumps(row))
     out = os.environ.get("PCR_PRECISION_OUT")
     if out:
