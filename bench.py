@@ -59,6 +59,10 @@ def _workload(name: str):
             scenes.shuffle(out, 17)
         return dict(desc="LIDAR 100M points, shuffled order, 1920x1080, 40-bit linear depth, eps 1%", n=100_000_000,
                     gen=gen, view=scenes.lidar_1km_view())
+    if name == "lidar20m":  # the same recipe and view at 20M points (320 MB, above L2): for profiler captures
+        return dict(desc="LIDAR 20M points (the 100M recipe at 20M points), 1920x1080, fov 60, near 0.1, far 3000, "
+                         "40-bit linear depth, eps 1%",
+                    n=20_000_000, gen=lambda n, out: scenes.lidar(n, 2, out=out), view=scenes.lidar_1km_view())
     if name == "cube1m":
         return dict(desc="1M points uniform in the unit cube, 640x480, fov 60, near 0.1, far 10, 40-bit linear depth",
                     n=1_000_000, gen=lambda n, out: scenes.cube(n, 1, out=out), view=scenes.cube_1m_view())
@@ -192,14 +196,29 @@ def cpu_oracle_frame(points, view, eps=(1, 100)):
     return time.perf_counter() - t0
 
 
+def _config(wl, args, n, world=1):
+    """The workload's config block, the same for both arms (the reference arm names its own point count)."""
+    view = wl["view"]
+    return {"workload": wl["desc"], "points": n, "width": view.width, "height": view.height,
+            "transform": args.transform,
+            "step": "atomicMin pass + basic resolve + HQ band pass + HQ resolve with clear",
+            "l2": f"inputs {wl['n'] * 16 / 1e9:.2f} GB > 129 MB L2: no flush between steps",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
+# The reference arm's work bound: point-frames over the whole run (warm-up included), about 50 s of the
+# oracle on one Grace core. The driver's short runs (about 25 frames) then take the full workload.
+REFERENCE_POINT_FRAMES = 3_000_000_000
+
+
 def run_reference(args, wl):
-    """The oracle as it stands, on host cores, on a bounded sample of the workload per step."""
+    """The oracle as it stands, on host cores: the workload's full point count when the run's frames fit the
+    work bound, else a bounded sample of it (the scene generated at fewer points, same recipe and view)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    # bounded work: at most about 3e9 point-frames over the whole run (about a minute at the default 600
-    # steps), so that the oracle's per-frame cost (clear and resolve of every pixel) stays small per point
-    sample_n = min(wl["n"], args.reference_sample, max(1_000_000, 3_000_000_000 // max(1, args.steps)))
+    cap = args.reference_sample if args.reference_sample else wl["n"]
+    sample_n = min(wl["n"], cap, max(1_000_000, REFERENCE_POINT_FRAMES // max(1, args.steps + args.warmup)))
     pts = np.empty((sample_n, 4), np.uint32)
     wl["gen"](sample_n, pts)
     for _ in range(args.warmup):
@@ -207,13 +226,16 @@ def run_reference(args, wl):
     ts = [cpu_oracle_frame(pts, wl["view"]) for _ in range(args.steps)]
     t = sum(ts) / len(ts)
     value = sample_n / t / 1e9
-    sample = (f"the workload's scene generated at {sample_n} points (same recipe and view), full frame: both "
-              f"passes and resolves")
+    if sample_n == wl["n"]:
+        sample = "the full workload (every point), full frame: both passes and resolves"
+    else:
+        sample = (f"the workload's scene generated at {sample_n} points (same recipe and view), full frame: both "
+                  f"passes and resolves")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "Gpts/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl["desc"], "points_per_step": sample_n},
+        "config": _config(wl, args, sample_n, args.gpus),
         "cpu_baseline": {"value": value, "unit": "Gpts/s", "cores": 1, "kind": "oracle", "sample": sample,
                          "host": host_cpu()},
         "e2e": {"value": value, "unit": "Gpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
@@ -349,6 +371,18 @@ def run_ours(args, wl):
     t_rd = timed(lambda: ceil.pcr_ceiling_stream_read(ctypes.c_void_p(pts.data_ptr()), n,
                                                       ctypes.c_void_p(sink.data_ptr()), s_ptr))
     read_gbs = n * BYTES_PER_POINT / (t_rd * 1e-3) / 1e9
+    # FP64 and FP32 fused multiply-add rates: the FP64 rate bounds a direct FP64 evaluation of the transform
+    ceil.pcr_ceiling_fma.argtypes = [ctypes.c_int32, ctypes.c_uint32, ctypes.c_void_p,
+                                     ctypes.POINTER(ctypes.c_uint64), ctypes.c_void_p]
+    fmas = ctypes.c_uint64()
+
+    def fma_rate(fp64, iters):
+        t = timed(lambda: ceil.pcr_ceiling_fma(fp64, iters, ctypes.c_void_p(sink.data_ptr()), ctypes.byref(fmas),
+                                               s_ptr))
+        return fmas.value / (t * 1e-3)
+
+    dfma_rate = fma_rate(1, 2000)
+    ffma_rate = fma_rate(0, 100000)
     del slots
     pattern = pattern_ceilings(ceil, pts, n, view, npx, eps, stream, timed)
 
@@ -407,9 +441,21 @@ def run_ours(args, wl):
         b.record(stream)
         torch.cuda.synchronize()
         e2e_ms = max_over_ranks(a.elapsed_time(b) / args.steps, dist, dev)
+        # the host-to-device link rate on this machine: one plain copy of the pinned points (best of 3)
+        link = 0.0
+        for _ in range(3):
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            d_pts2[1].copy_(host, non_blocking=True)
+            c1.record(stream)
+            c1.synchronize()
+            link = max(link, n * BYTES_PER_POINT / (c0.elapsed_time(c1) * 1e-3) / 1e9)
+        link_ms = n * BYTES_PER_POINT / (link * 1e9) * 1e3
         e2e = {"value": job_rate(n, world, e2e_ms) / 1e9, "unit": "Gpts/s", "ms_per_step": e2e_ms,
                "h2d_bytes_per_step": n * BYTES_PER_POINT, "d2h_bytes_per_step": 2 * npx * 4,
-               "api": "pcr_render_frame_host, 2 frames in flight"}
+               "api": "pcr_render_frame_host, 2 frames in flight",
+               # bound: the points' upload at the measured pinned host-to-device copy rate
+               "h2d_link_gbs": link, "h2d_link_ms": link_ms, "frac_of_link": link_ms / e2e_ms}
         fbs2[1].close()
 
     if rank != 0:
@@ -432,10 +478,7 @@ def run_ours(args, wl):
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"exact": "f32+i64+f64", "fp64": "f64", "double-float": "f32"}[args.transform],
         "data": "synthetic",
-        "config": {"workload": wl["desc"], "points": n, "width": W, "height": H, "transform": args.transform,
-                   "step": "atomicMin pass + basic resolve + HQ band pass + HQ resolve with clear",
-                   "l2": "inputs 1.6 GB > 129 MB L2: no flush between steps",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "config": _config(wl, args, n, world),
         "kernels_ms": per_kernel,
         "atomicmin_gpts": pass1_pts / 1e9,
         "hq_splat_gpts": n / ((per_kernel["raster_atomicmin"] + per_kernel["hq_accumulate"] +
@@ -447,7 +490,8 @@ def run_ours(args, wl):
             "floor": "max(16 B/point at the measured HBM peak, the pass's framebuffer operations for this cloud "
                      "and view replayed alone in point order without the transform; pass 1: the faster of one "
                      "atomic per fragment and a stored-key read that skips atomics which cannot lower it)",
-            "random_u64_atomics_per_s": atomic_rate, "stream_read_gbs": read_gbs, **pattern,
+            "random_u64_atomics_per_s": atomic_rate, "fp64_dfma_per_s": dfma_rate, "fp32_ffma_per_s": ffma_rate,
+            "stream_read_gbs": read_gbs, **pattern,
             "atomicmin_floor_ms": floor1, "hq_accumulate_floor_ms": floor2,
             "atomicmin_frac_of_floor": floor1 / per_kernel["raster_atomicmin"],
             "hq_accumulate_frac_of_floor": floor2 / per_kernel["hq_accumulate"],
@@ -723,7 +767,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=100_000_000)
-    ap.add_argument("--reference-sample", type=int, default=20_000_000)
+    ap.add_argument("--reference-sample", type=int, default=0,
+                    help="reference arm: at most this many points per frame (0: the workload's own count)")
     ap.add_argument("--requests", type=int, default=2000, help="serving workload: number of requests")
     ap.add_argument("--views", type=int, default=64, help="batched workload: number of orbit poses")
     ap.add_argument("--points", type=int, default=20_000_000, help="batched workload: cloud size")

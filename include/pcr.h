@@ -98,6 +98,10 @@ typedef struct {
                                (in pass 1 only where the fragment's key is below the key the pixel holds) */
   int32_t blocks_per_sm;    /* 256-thread blocks per SM for the point passes, 1..32 (default 8; capped at the
                                blocks that can be resident, 4 for pass 1 and 5 for pass 2) */
+  int32_t staging;          /* how each warp brings its tiles of 64 points in: 0 (default) its own 16-byte
+                               loads, one tile ahead; 1 bulk copies (cp.async.bulk) into a two-stage
+                               shared-memory ring whose waits are bounded (a wait that gives up sets the
+                               timeout status, see pcr_get_device_status) */
 } pcr_tuning;
 
 /* Framebuffer flags. */

@@ -3,6 +3,7 @@
  * The rasterizer of arXiv 1908.02681 (Section 2.1) is bound by reading 16-byte points from memory and
  * by 64-bit atomic minima into a framebuffer that lives in L2. These probes measure the two ceilings
  * on the running GPU; the benchmark times them with CUDA events and reports its kernels against them.
+ * A third probe measures the FP64 and FP32 fused multiply-add rates that bound the per-point transform.
  * The paper has no counterpart (it reports frame times only, Table 1).
  *
  * All pointers are caller-owned device memory; calls enqueue one kernel on `stream` and return
@@ -47,6 +48,13 @@ int pcr_ceiling_pattern_min(const uint32_t* d_pix, const uint64_t* d_key, uint64
                             void* stream);
 int pcr_ceiling_pattern_hq(const uint32_t* d_pix, const uint64_t* d_key, uint64_t n, const uint64_t* d_keys,
                            uint64_t* d_accum, uint32_t eps_num, uint32_t eps_den, uint64_t nq, void* stream);
+
+/* Fused multiply-add throughput of the FP64 (fp64 = 1) or FP32 (fp64 = 0) pipes: sms * 8 blocks of 256
+ * threads, each running 8 independent chains of `iters` explicitly rounded fmas. *fmas receives the total
+ * number of fmas enqueued (host memory); divide by the kernel's time for the rate. The FP64 rate is what a
+ * direct FP64 evaluation of the per-point transform (Sections 1 and 2.1: depth in double precision) is
+ * bound by. d_sink must hold sms * 8 * 256 u32; iters >= 1. */
+int pcr_ceiling_fma(int32_t fp64, uint32_t iters, uint32_t* d_sink, uint64_t* fmas, void* stream);
 
 #ifdef __cplusplus
 }

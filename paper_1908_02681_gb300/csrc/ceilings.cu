@@ -1,5 +1,5 @@
-// Roofline probes (include/pcr_ceilings.h): random u64 L2 atomics, 16-byte streaming reads, and the passes'
-// framebuffer operations replayed without the transform.
+// Roofline probes (include/pcr_ceilings.h): random u64 L2 atomics, 16-byte streaming reads, the passes'
+// framebuffer operations replayed without the transform, and the FP64 / FP32 fused multiply-add rates.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -89,6 +89,33 @@ __global__ void __launch_bounds__(256) k_pattern_hq(const uint32_t* __restrict__
   }
 }
 
+// Fused multiply-add throughput: every thread runs kFmaChains independent chains of `iters` fmas each
+// (explicitly rounded, so nothing is contracted or folded), then writes to sink only when the sum hits an
+// impossible value. The chains hide the pipe latency at full occupancy.
+constexpr int kFmaChains = 8;
+constexpr int kFmaThreads = 256;
+constexpr int kFmaBlocksPerSm = 8;
+
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+template <typename T>
+__global__ void __launch_bounds__(kFmaThreads) k_fma(uint32_t iters, uint32_t* sink) {
+  T a[kFmaChains];
+#pragma unroll
+  for (int k = 0; k < kFmaChains; ++k) a[k] = (T)(threadIdx.x + 1 + k) * (T)0.001;
+  const T b = (T)0.9999, c = (T)0.0001;
+#pragma unroll 1
+  for (uint32_t i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < kFmaChains; ++k) a[k] = fma_rn(a[k], b, c);
+  }
+  T s = (T)0;
+#pragma unroll
+  for (int k = 0; k < kFmaChains; ++k) s += a[k];
+  if (s == (T)-1.0) sink[(uint64_t)blockIdx.x * blockDim.x + threadIdx.x] = 1u;
+}
+
 int sms() {
   int dev = 0, v = 1;
   cudaGetDevice(&dev);
@@ -155,5 +182,16 @@ extern "C" int pcr_ceiling_pattern_hq(const uint32_t* d_pix, const uint64_t* d_k
       d_pix, reinterpret_cast<const unsigned long long*>(d_key), n,
       reinterpret_cast<const unsigned long long*>(d_keys), reinterpret_cast<unsigned long long*>(d_accum), eps_num,
       eps_den, nq);
+  return (int)cudaGetLastError();
+}
+
+extern "C" int pcr_ceiling_fma(int32_t fp64, uint32_t iters, uint32_t* d_sink, uint64_t* fmas, void* stream) {
+  if (!d_sink || !fmas || (fp64 != 0 && fp64 != 1) || iters == 0) return (int)cudaErrorInvalidValue;
+  const unsigned grid = (unsigned)(sms() * kFmaBlocksPerSm);
+  *fmas = (uint64_t)grid * kFmaThreads * kFmaChains * iters;
+  if (fp64)
+    k_fma<double><<<grid, kFmaThreads, 0, (cudaStream_t)stream>>>(iters, d_sink);
+  else
+    k_fma<float><<<grid, kFmaThreads, 0, (cudaStream_t)stream>>>(iters, d_sink);
   return (int)cudaGetLastError();
 }

@@ -281,8 +281,10 @@ pcr_status pcr_set_tuning(pcr_framebuffer* fb, const pcr_tuning* tuning) {
   if (tuning->merge_same_pixel != 0 && tuning->merge_same_pixel != 1)
     return fail(PCR_ERR_INVALID_ARG, "merge_same_pixel must be 0 or 1");
   if (tuning->blocks_per_sm < 1 || tuning->blocks_per_sm > 32) return fail(PCR_ERR_INVALID_ARG, "blocks_per_sm must be in 1..32");
+  if (tuning->staging != 0 && tuning->staging != 1) return fail(PCR_ERR_INVALID_ARG, "staging must be 0 or 1");
   fb->tuning.merge = tuning->merge_same_pixel;
   fb->tuning.blocks_per_sm = tuning->blocks_per_sm;
+  fb->tuning.staging = tuning->staging;
   return PCR_OK;
 }
 
@@ -291,6 +293,7 @@ pcr_status pcr_get_tuning(const pcr_framebuffer* fb, pcr_tuning* tuning) {
   if (!tuning) return fail(PCR_ERR_INVALID_ARG, "tuning is NULL");
   tuning->merge_same_pixel = fb->tuning.merge;
   tuning->blocks_per_sm = fb->tuning.blocks_per_sm;
+  tuning->staging = fb->tuning.staging;
   return PCR_OK;
 }
 
@@ -346,6 +349,7 @@ pcr_status pcr_autotune(pcr_framebuffer* fb, const pcr_point* d_points, uint64_t
   if (st == PCR_OK && best) {
     best->merge_same_pixel = fb->tuning.merge;
     best->blocks_per_sm = fb->tuning.blocks_per_sm;
+    best->staging = fb->tuning.staging;
   }
   return st;
 }

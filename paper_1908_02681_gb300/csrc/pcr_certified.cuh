@@ -50,14 +50,15 @@ constexpr int kFixedFracBits = 40;             // t is held in units of 2^-40
 struct CertParams {
   // hot scalars first: the per-point loops read them as instruction operands; the table comes last
   float H[3][4], L[3][4];             // float splits of the rows clip x, clip y, w (H: nearest float, L: rest)
-  float delta_c;                      // |float(clip) - fma-chain estimate| <= delta_c * T (per row)
-  float d_k1, d_k2;                   // tier-1 bound of t: D = d_k1 * T_w + d_k2
-  float half_d;                       // RD(1/2 - d_k2 - 2^-22): tier 1 tests |frac - 1/2| < half_d - d_k1 T_w
-  float k1_c, k2_c;                   // tier-1 pixel bound factors 0.506 (1 + 1e-6), 0.506 delta_c (1 + 1e-6)
-  float hw, hwm, hh, hhm, wm, hm;     // W/2, W/2 - 1/2, H/2, H/2 - 1/2, W - 1/2, H - 1/2 (exact)
-  float HM[4];                        // per column, the largest |H| over the three rows
-  float near_in, far_in;              // w - dw > near_in => w >= near; w + dw < far_in => w < far (FP64 w)
-  float near_out, far_out;            // w + dw < near_out => w < near; w - dw > far_out => w >= far
+  // tier 1 (classify_fast); s = |x| + |y| + |z| of the point, evaluated in float
+  float Wr[4];                        // w row, nearest floats of M[3][c]
+  float Gx[4], Gy[4];                 // nearest floats of W/2 M[0] + (W/2 - 1/2) M[3], H/2 M[1] + (H/2 - 1/2) M[3]
+  float wc, whk, kw, kw3;             // depth window: |w - wc| < whk - kw s certifies near <= w_FP64 < far
+  float near_o, far_o;                // RD(near), RU(far): w + dw < near_o or w - dw >= far_o culls
+  float ke, ke3, he0;                 // pixel bound: hE = he0 - (ke s + ke3) / w <= 1/2 - E
+  float kd, hd0;                      // depth code: hD = hd0 - kd s <= 1/2 - D - 2^-22 + 2^-25
+  float Mw, Mw3, MH, MH3, cb, ce;     // cull branch: magnitude sums and the general pixel bound
+  float wm, hm;                       // W - 1/2, H - 1/2 (exact)
   float xyz_max;                      // |x| + |y| + |z| below this: table entries usable, values finite
   float kappa;                        // double-float error bound factor (relative to T)
   float t_c1, t_c2;                   // tier-2 bound of t: t_c1 * T_t + t_c2
@@ -77,42 +78,44 @@ struct CertParams {
 
 // The first-tier constants of one view (a subset of CertParams with the same field names).
 struct HotParams {
-  float H[3][4];
-  float HM[4];
-  float delta_c, d_k1, half_d, k1_c, k2_c, hw, hwm, hh, hhm, wm, hm, near_in, far_in, near_out, far_out, xyz_max;
+  float Wr[4], Gx[4], Gy[4];
+  float wc, whk, kw, kw3, near_o, far_o, ke, ke3, he0, kd, hd0, Mw, Mw3, MH, MH3, cb, ce, wm, hm, xyz_max;
   unsigned long long BL;
   long long BH;
   struct {
-    float fwidth, fheight;
     int32_t width, height;
   } v;
 };
 
 __host__ __device__ inline HotParams hot_params(const CertParams& P) {
   HotParams h;
-  for (int r = 0; r < 3; ++r)
-    for (int c = 0; c < 4; ++c) h.H[r][c] = P.H[r][c];
-  for (int c = 0; c < 4; ++c) h.HM[c] = P.HM[c];
-  h.delta_c = P.delta_c;
-  h.d_k1 = P.d_k1;
-  h.half_d = P.half_d;
-  h.k1_c = P.k1_c;
-  h.k2_c = P.k2_c;
-  h.hw = P.hw;
-  h.hwm = P.hwm;
-  h.hh = P.hh;
-  h.hhm = P.hhm;
+  for (int c = 0; c < 4; ++c) {
+    h.Wr[c] = P.Wr[c];
+    h.Gx[c] = P.Gx[c];
+    h.Gy[c] = P.Gy[c];
+  }
+  h.wc = P.wc;
+  h.whk = P.whk;
+  h.kw = P.kw;
+  h.kw3 = P.kw3;
+  h.near_o = P.near_o;
+  h.far_o = P.far_o;
+  h.ke = P.ke;
+  h.ke3 = P.ke3;
+  h.he0 = P.he0;
+  h.kd = P.kd;
+  h.hd0 = P.hd0;
+  h.Mw = P.Mw;
+  h.Mw3 = P.Mw3;
+  h.MH = P.MH;
+  h.MH3 = P.MH3;
+  h.cb = P.cb;
+  h.ce = P.ce;
   h.wm = P.wm;
   h.hm = P.hm;
-  h.near_in = P.near_in;
-  h.far_in = P.far_in;
-  h.near_out = P.near_out;
-  h.far_out = P.far_out;
   h.xyz_max = P.xyz_max;
   h.BL = P.BL;
   h.BH = P.BH;
-  h.v.fwidth = P.v.fwidth;
-  h.v.fheight = P.v.fheight;
   h.v.width = P.v.width;
   h.v.height = P.v.height;
   return h;
@@ -159,6 +162,107 @@ inline bool split_float(double m, float* h, float* l) {
 inline void two_float(double x, float* h, float* l) {
   *h = (float)x;
   *l = (float)(x - (double)*h);
+}
+
+// float rounded up / down from a double (directed conversion: the nearest float, moved one step if it
+// lies on the wrong side)
+inline float f_up(double x) {
+  float f = (float)x;
+  if ((double)f < x) f = std::nextafter(f, 3.4e38f);
+  return f;
+}
+inline float f_down(double x) {
+  float f = (float)x;
+  if ((double)f > x) f = std::nextafter(f, -3.4e38f);
+  return f;
+}
+
+// Constants of tier 1 (classify_fast). Notation: u = 2^-24, v = 2^-53, a = |x| + |y| + |z| of the point, s its
+// float evaluation (two roundings: a <= s (1 + 2.0001u)); T_R = sum_c |R_c x_c| + |R_3| for a row R; w*, cx*, cy*
+// the exact clip values of the point and w_d, cx_d, cy_d the FP64 definition's.
+//   * w estimate wf: float fma chain of the nearest floats of M[3]: |wf - w*| <= 4.0003u T_M3 (one rounding per
+//     entry, three fmas); |w_d - w*| <= 3.0001v T_M3. With T_M3 <= Mw s + Mw3, Delta = kw s + kw3 bounds both.
+//   * pixel: G = W/2 M[0] + (W/2 - 1/2) M[3] gives G . p = w* (fx* - 1/2), fx* the exact pixel coordinate. The
+//     estimate fm = gx * rcp(wf) (gx the fma chain of G's nearest floats; rcp.approx within 2^-23) satisfies
+//     |fm - F| <= 3.0002u |fm| + g + b |F|, F = fx* - 1/2, g = 4.001u T_H / wf, b = 4.001u T_M3 / wf,
+//     T_H = sum_c (W/2 |M0c| + (W/2 - 1/2) |M3c|) |x_c| + ... The definition's own float roundings (division,
+//     fma, product by W) and FP64 errors add |fx_d - fx*| <= 3.0002u (W/2) |nd*| + 2.0001u |fx*| + 2^-22 (the
+//     FP64 part is below 2^-28 (g + b (W + 1))). For a point certified inside the image (|fm| < W, and the
+//     bound below under 1/2, which gives |F| <= W + 1/2), E = |fx_d - 1/2 - fm| <= u (6.51 M + 3.51) + g +
+//     b (M + 1) + 2^-22, M = max(W, H); the same for y with H.
+//   * depth code: |t_FP64 - t| <= v (5.2 T_t + 3.1 S near) (see prepare_cert), T_t <= S (M3max a + |M3_3| +
+//     near); the fixed-point sum adds < 2^-15.
+inline bool tier1_constants(const DevView& v, double S, CertParams* P) {
+  const double u = 0x1p-24, v53 = 0x1p-53;
+  const double W = v.width, Hd = v.height, M = W > Hd ? W : Hd;
+  const double hw = 0.5 * W, hwm = 0.5 * W - 0.5, hh = 0.5 * Hd, hhm = 0.5 * Hd - 0.5;
+  const double *m0 = v.m, *m1 = v.m + 4, *m3 = v.m + 8;
+  double m3max = 0.0, hmax = 0.0;
+  for (int c = 0; c < 4; ++c) {
+    const double gx = std::fma(hw, m0[c], hwm * m3[c]), gy = std::fma(hh, m1[c], hhm * m3[c]);
+    // every entry a normal float or zero (so its rounding is relative) and finite
+    for (double g : {gx, gy, m3[c]})
+      if (!(std::fabs(g) < 3.0e38) || (g != 0.0 && std::fabs(g) < 0x1p-100)) return false;
+    P->Wr[c] = (float)m3[c];
+    P->Gx[c] = (float)gx;
+    P->Gy[c] = (float)gy;
+    if (c < 3) {
+      m3max = std::fmax(m3max, std::fabs(m3[c]));
+      hmax = std::fmax(hmax, std::fmax(hw * std::fabs(m0[c]) + hwm * std::fabs(m3[c]),
+                                       hh * std::fabs(m1[c]) + hhm * std::fabs(m3[c])));
+    }
+  }
+  const double h3 = std::fmax(hw * std::fabs(m0[3]) + hwm * std::fabs(m3[3]), hh * std::fabs(m1[3]) + hhm * std::fabs(m3[3]));
+  // magnitude sums in s: T_M3 <= (Mw s + Mw3) / (1 + 2^-20), T_H <= (MH s + MH3) / (1 + 2^-20)
+  const double sl = (1.0 + 2.0001 * u) * (1.0 + 0x1p-20);
+  P->Mw = f_up(m3max * sl);
+  P->Mw3 = f_up(std::fabs(m3[3]) * (1.0 + 0x1p-20));
+  P->MH = f_up(hmax * sl);
+  P->MH3 = f_up(h3 * (1.0 + 0x1p-20));
+  // depth window: |wf - wc| < RN(whk - kw s) gives |wf - wc| + Delta < wh, with (wc - wh, wc + wh) inside
+  // [near_in, far_in]; near_in also keeps t >= 2.5 and far_in keeps t <= 2^40 - 2^25, so the tier-1 code of a
+  // point certified visible needs no sign, zero or cap check (t = S (w - near) or S w). The (1 -+ 4u) margins
+  // are kept from the FP64 rounding of t near those ends.
+  {
+    const double t_lo = 2.5, t_hi = 1099511627776.0 - 33554432.0;
+    const double w_lo = P->linear ? v.near_ + t_lo / S : t_lo / S;
+    const double w_hi = P->linear ? v.near_ + t_hi / S : t_hi / S;
+    const double nin = std::fmax(v.near_ * (1.0 + 4.0 * u), w_lo * (1.0 + 4.0 * u));
+    const double fin = std::fmin(v.far_ * (1.0 - 4.0 * u), w_hi * (1.0 - 4.0 * u));
+    P->kw = f_up(4.0004 * u * (double)P->Mw * (1.0 + 0x1p-20));
+    P->kw3 = f_up(4.0004 * u * (double)P->Mw3 * (1.0 + 0x1p-20));
+    if (fin > nin) {
+      P->wc = (float)(0.5 * (nin + fin));
+      const double wh = std::fmin((double)P->wc - nin, fin - (double)P->wc);
+      const double whk = (wh - (double)P->kw3) / (1.0 + 2.0001 * u);
+      P->whk = whk > 0.0 ? f_down(whk) : 0.0f;  // 0: tier 1 never certifies the depth
+    } else {
+      P->wc = 0.0f;
+      P->whk = 0.0f;
+    }
+  }
+  P->near_o = f_down(v.near_);
+  P->far_o = f_up(v.far_);
+  // pixel bound of a visible point: (ke s + ke3) / wf >= g + b (M + 1) (with the roundings of s, the fma, the
+  // reciprocal and the product folded into the 1 + 2^-19); he0 = 1/2 - u (6.51 M + 3.51) - 2^-22 - 2^-24, the
+  // 2^-24 covering the rounding of hE itself (below 2^-25)
+  const double cE = 4.001 * u * (1.0 + 0x1p-19);
+  P->ke = f_up(cE * ((double)P->MH + (M + 1.0) * (double)P->Mw));
+  P->ke3 = f_up(cE * ((double)P->MH3 + (M + 1.0) * (double)P->Mw3));
+  P->he0 = f_down(0.5 - u * (6.51 * M + 3.51) - 0x1p-22 - 0x1p-24);
+  // cull branch: b and g from the same sums; E <= |fm| (9.67u + 1.3338 b) + 1.335 g + 3.02u max(W/2 - 1/2,
+  // H/2 - 1/2) + 2^-21 for any |fm| when b <= 1/4 (the kernel uses 9.8u, 1.35 and ce)
+  P->cb = f_up(4.001 * u * (1.0 + 0x1p-19));
+  P->ce = f_up(3.05 * u * std::fmax(hwm, hhm) + 0x1p-20);
+  P->wm = (float)(W - 0.5);
+  P->hm = (float)(Hd - 0.5);
+  // depth code: D <= kd s + d0; hD = RN(hd0 - kd s) with hd0 = RD(1/2 - d0 - 2^-22) (the 2^-22 covers the
+  // 23-bit truncation of the fraction and the rounding of that fma)
+  P->kd = f_up(5.2 * v53 * S * m3max * (1.0 + 2.0001 * u) * (1.0 + 0x1p-18));
+  const double nl = P->linear ? v.near_ : 0.0;
+  const double d0 = 5.2 * v53 * S * (std::fabs(m3[3]) + nl) * (1.0 + 0x1p-18) + 3.1 * v53 * S * nl + 0x1p-13;
+  P->hd0 = f_down(0.5 - d0 - 0x1p-22);
+  return true;
 }
 
 // Fills P for the view; false when the view is outside the certified evaluation's preconditions (the
@@ -219,47 +323,7 @@ inline bool prepare_cert(const DevView& v, bool approximate, CertParams* P) {
   const double u64 = 0x1p-53;
   P->t_c1 = (float)(5.2 * u64 * (1.0 + 0x1p-18));
   P->t_c2 = (float)((P->linear ? 3.1 * u64 * S * v.near_ : 0.0) + 0x1p-13);
-  // tier 1: T_t <= S (1 + u) T_w + S near (LINEAR), with T_w the float fma-chain magnitude of the w row
-  // (>= (1 - 3u) times the exact one): D = c1 (S (1 + 8u) T_w + S near) + c2
-  const double uf = 0x1p-24;
-  P->d_k1 = (float)(5.2 * u64 * S * (1.0 + 8.0 * uf) * (1.0 + 0x1p-18));
-  P->d_k2 = (float)(5.2 * u64 * (P->linear ? S * v.near_ : 0.0) + (double)P->t_c2);
-  // |RN32(clip_FP64) - fma-chain estimate| <= (u + 4u + 3 u64) T_H, T_H <= (1 + 3u) T_computed
-  P->delta_c = (float)(5.1 * uf);
-  // 1/2 - d_k2 - 2^-22, rounded down (the 2^-22 covers the 23-bit truncation of the fraction and the rounding
-  // of the fma that subtracts d_k1 T_w; see classify_fast)
-  {
-    const double hd = 0.5 - (double)P->d_k2 - 0x1p-22;
-    float f = (float)hd;
-    if ((double)f > hd) f = std::nextafter(f, -1.0f);
-    P->half_d = f;
-  }
-  // fx bound factors (see classify_fast): 0.506 and 0.506 delta_c, times 1 + 1e-6 for the approximate
-  // reciprocal of w - dw, rounded up
-  P->k1_c = std::nextafter((float)(0.506 * (1.0 + 1e-6)), 1.0f);
-  P->k2_c = std::nextafter((float)(0.506 * (double)P->delta_c * (1.0 + 1e-6)), 1.0f);
-  for (int c = 0; c < 4; ++c)
-    P->HM[c] = std::fmax(std::fmax(std::fabs(P->H[0][c]), std::fabs(P->H[1][c])), std::fabs(P->H[2][c]));
-  P->hw = 0.5f * v.fwidth;
-  P->hwm = 0.5f * v.fwidth - 0.5f;
-  P->hh = 0.5f * v.fheight;
-  P->hhm = 0.5f * v.fheight - 0.5f;
-  P->wm = v.fwidth - 0.5f;
-  P->hm = v.fheight - 0.5f;
-  // float clip-plane thresholds with (1 +- 4u) margins for the rounding of w -+ dw
-  // near_in also keeps t >= 2.5 and far_in keeps t <= 2^40 - 2^25 for w between them, so the tier-1 code of a
-  // point it certifies as visible needs no sign, zero or cap check (t = S (w - near) or S w)
-  {
-    const double t_lo = 2.5, t_hi = 1099511627776.0 - 33554432.0;
-    const double w_lo = P->linear ? v.near_ + t_lo / S : t_lo / S;
-    const double w_hi = P->linear ? v.near_ + t_hi / S : t_hi / S;
-    const double nin = std::fmax(v.near_ * (1.0 + 4.0 * uf), w_lo * (1.0 + 4.0 * uf));
-    const double fin = std::fmin(v.far_ * (1.0 - 4.0 * uf), w_hi * (1.0 - 4.0 * uf));
-    P->near_in = std::nextafter((float)nin, 3.0e38f);
-    P->far_in = std::nextafter((float)fin, 0.0f);
-  }
-  P->near_out = std::nextafter((float)(v.near_ * (1.0 - 4.0 * uf)), 0.0f);
-  P->far_out = std::nextafter((float)(v.far_ * (1.0 + 4.0 * uf)), 3.0e38f);
+  if (!tier1_constants(v, S, P)) return false;
   {
     int emin = 254;
     for (int j = 0; j < 3; ++j) emin = P->e_max[j] < emin ? P->e_max[j] : emin;
@@ -443,30 +507,24 @@ __device__ __forceinline__ unsigned long long code_from_fixed(uint32_t a1, uint3
 }
 
 // Tier 1: the exact depth code from the fixed-point row (two 64-bit multiply-add accumulators), the cull
-// from the float w estimate and its bound, and a float pixel estimate with a rigorous per-point bound.
-// Written without early exits: every quantity is computed for every point (a non-finite coordinate
-// only produces NaN or infinity, which every decision below treats as undecided), and the state is
-// assembled from predicates at the end.
+// from the float w estimate and its bound, and a float pixel estimate with a rigorous per-point bound (the
+// constants and their derivation: tier1_constants). All bounds share one magnitude sum s = |x| + |y| + |z|;
+// the pixel estimate fm = fx - 1/2 comes from one fma chain per axis (the pixel mapping folded into the clip
+// row) and one reciprocal of w. The visible case is decided from predicates without early exits (a
+// non-finite coordinate only produces NaN or infinity, which every decision treats as undecided); only a
+// point it does not certify takes the branch that tests whether it is certainly culled.
 // PP: CertParams (single-view kernels, read from the kernel parameter block) or HotParams (batched
 // kernels, which hold one view's first-tier constants in registers); both have the fields used here.
 template <typename PP>
 __device__ __forceinline__ FastFrag classify_fast(const PP& P, const long long* __restrict__ F, uint4 p) {
   const float x = __uint_as_float(p.x), y = __uint_as_float(p.y), z = __uint_as_float(p.z);
-  // finite, and inside the exponent range whose table entries exist (else tier 2 decides): the rounded sum
-  // of the magnitudes is at least each of them, and NaN or infinity fails the comparison
-  const bool in_range = __fadd_rn(__fadd_rn(fabsf(x), fabsf(y)), fabsf(z)) < P.xyz_max;
-  // float estimate of w (fma chain, as the FP64 definition orders it), and one term-magnitude sum T for all three
-  // rows: per column the largest |H| over the rows, so T is at least each row's own sum of |H_rc x_c| (computed
-  // by the same fma chain) and serves every row's error bound below. It costs one chain instead of three; the
-  // looser bound sends ~0.04 % more points to tier 2.
-  const float w = __fmaf_rn(P.H[2][2], z, __fmaf_rn(P.H[2][1], y, __fmaf_rn(P.H[2][0], x, P.H[2][3])));
-  const float Tw = __fmaf_rn(P.HM[2], fabsf(z), __fmaf_rn(P.HM[1], fabsf(y), __fmaf_rn(P.HM[0], fabsf(x), P.HM[3])));
-  const float dw = __fmul_rn(P.delta_c, Tw);
-  const float wlo = __fsub_rd(w, dw), whi = __fadd_ru(w, dw);  // directed: wlo <= w - dw, whi >= w + dw
-  // predicates combined with bitwise & and |: every operand is computed anyway, and this keeps the
-  // decision free of short-circuit branches
-  const bool depth_out = (whi < P.near_out) | (wlo > P.far_out);
-  const bool depth_in = (wlo > P.near_in) & (whi < P.far_in);
+  // finite, and inside the exponent range whose table entries exist (else tier 2 decides): the rounded sum of
+  // the magnitudes is at least each of them, and NaN or infinity fails the comparison
+  const float s = __fadd_rn(__fadd_rn(fabsf(x), fabsf(y)), fabsf(z));
+  const bool in_range = s < P.xyz_max;
+  // w estimate (fma chain, as the FP64 definition orders it) and the depth window: |w - wc| + Delta < wh
+  const float w = __fmaf_rn(P.Wr[2], z, __fmaf_rn(P.Wr[1], y, __fmaf_rn(P.Wr[0], x, P.Wr[3])));
+  const bool depth_in = fabsf(__fsub_rn(w, P.wc)) < __fmaf_rn(-P.kw, s, P.whk);
   // ---- depth code: t * 2^40 = sum m_j F_j + B, accumulated as sum m_j F_lo_j + 2^32 sum m_j F_hi_j
   const long long fx_ = F[p.x >> 23], fy_ = F[kTableEntries + (p.y >> 23)], fz_ = F[2 * kTableEntries + (p.z >> 23)];
   const uint32_t mx = (p.x & 0x7FFFFFu) | 0x800000u, my = (p.y & 0x7FFFFFu) | 0x800000u,
@@ -486,65 +544,52 @@ __device__ __forceinline__ FastFrag classify_fast(const PP& P, const long long* 
       : "r"((uint32_t)(L >> 32)), "r"((uint32_t)Hh), "r"((uint32_t)((unsigned long long)Hh >> 32)));
   const float frac =
       __fsub_rn(__uint_as_float(0x3F800000u | (__funnelshift_r(out.a0, out.a1, 17) & 0x7FFFFFu)), 1.0f);
-  // The code is floor(t_FP64) when D < frac_exact < 1 - D, D = d_k1 T_w + d_k2 (the FP64 rounding and the
+  // The code is floor(t_FP64) when D < frac_exact < 1 - D, D <= kd s + d0 (the FP64 rounding and the
   // fixed-point sum's error). frac is the fraction truncated to 23 bits (frac <= frac_exact < frac + 2^-23).
-  // hD = RN(half_d - d_k1 T_w), half_d = RD(1/2 - d_k2 - 2^-22), is within 2^-25 of its real value, so
-  // |frac - 1/2| < hD (frac - 1/2 is exact) gives D + 2^-22 - 2^-25 < frac and frac + 2^-23 < 1 - D.
-  // hD > 1/4 gives D < 1/4: an undecided code still has two usable candidates.
-  const float hD = __fmaf_rn(-P.d_k1, Tw, P.half_d);
+  // hD = RN(hd0 - kd s), hd0 = RD(1/2 - d0 - 2^-22), is within 2^-25 of its real value, so |frac - 1/2| < hD
+  // (frac - 1/2 is exact) gives D + 2^-22 - 2^-25 < frac and frac + 2^-23 < 1 - D. hD > 1/4 gives D < 1/4:
+  // an undecided code still has two usable candidates.
+  const float hD = __fmaf_rn(-P.kd, s, P.hd0);
   const bool exact = fabsf(__fsub_rn(frac, 0.5f)) < hD;
   out.lo_half = frac < 0.5f;
   const bool amb_ok = hD > 0.25f;
-  // ---- pixel estimate
-  const float cx = __fmaf_rn(P.H[0][2], z, __fmaf_rn(P.H[0][1], y, __fmaf_rn(P.H[0][0], x, P.H[0][3])));
-  const float Tx = Tw;
-  const float cy = __fmaf_rn(P.H[1][2], z, __fmaf_rn(P.H[1][1], y, __fmaf_rn(P.H[1][0], x, P.H[1][3])));
-  const float Ty = Tw;
-  // with wlo > near_in > 0: rcp.approx (relative error <= 2^-23); r0 (1 + 1e-6) >= 1 / (w - dw), and the
-  // factor 1 + 1e-6 is folded into k1_c and k2_c
-  const float rw = rcp_approx(w);
-  const float r0 = rcp_approx(wlo);
-  const float ndx = __fmul_rn(cx, rw), ndy = __fmul_rn(cy, rw);
-  // fm = fx - 1/2 for the pixel coordinate fx = (nd / 2 + 1/2) W, in one rounding: fm = RN(nd W/2 + (W/2 - 1/2))
-  const float fxm = __fmaf_rn(ndx, P.hw, P.hwm), fym = __fmaf_rn(ndy, P.hh, P.hhm);
-  // |fx_FP64 - fx| <= E = W ((3.52u + 0.506 rho') |nd| + 0.506 rden dc T + 2.13u (|nd| + 1)) + 2^-20 with
-  // rho' = rden dw (see the file header); |fx| <= W (|nd| + 1) / 2 folds the 4.25u |fx| term, and one
-  // rounding of fm (instead of two for fx) stays inside it. Tier 1 uses hE = RN(1/2 - 2^-19 - (E - 2^-20)),
-  // within 2^-25 of its real value, so hE < 1/2 - E - 2^-20 + 2^-25.
-  const float k1 = __fmaf_rn(P.k1_c, __fmul_rn(r0, dw), 5.65f * 0x1p-24f);
-  const float k2 = __fmul_rn(r0, P.k2_c);
-  const float hEx = __fmaf_rn(-P.v.fwidth, __fmaf_rn(k1, fabsf(ndx), __fmaf_rn(k2, Tx, 2.13f * 0x1p-24f)),
-                              0.5f - 0x1p-19f);
-  const float hEy = __fmaf_rn(-P.v.fheight, __fmaf_rn(k1, fabsf(ndy), __fmaf_rn(k2, Ty, 2.13f * 0x1p-24f)),
-                              0.5f - 0x1p-19f);
+  // ---- pixel estimate: gx = w (fx - 1/2), gy = w (fy - 1/2) up to the rounding bounds; with wf > 0 (depth_in)
+  // fm = g * rcp(wf) and the bound hE = RN(he0 - (ke s + ke3) rcp(wf)) <= 1/2 - E - 2^-25
+  const float gx = __fmaf_rn(P.Gx[2], z, __fmaf_rn(P.Gx[1], y, __fmaf_rn(P.Gx[0], x, P.Gx[3])));
+  const float gy = __fmaf_rn(P.Gy[2], z, __fmaf_rn(P.Gy[1], y, __fmaf_rn(P.Gy[0], x, P.Gy[3])));
+  const float r = rcp_approx(w);
+  const float fxm = __fmul_rn(gx, r), fym = __fmul_rn(gy, r);
+  const float hE = __fmaf_rn(-__fmaf_rn(P.ke, s, P.ke3), r, P.he0);
   // floor of fx = fm + 1/2 via the 1.5 * 2^23 shift: for -1/2 <= fm < 2^22 the sum lies in [2^23, 2^24), where
   // floats are the integers, so g rounds fm to the nearest integer k: floor(fx) unless fx is an integer (then
   // fx - 1 or fx, and |fm - k| = 1/2 fails the test below). Outside that range k, read from the bits, is
   // negative or above 2^22 as an unsigned number: never below the image size.
-  const float gx = __fadd_rn(fxm, 12582912.0f), gy = __fadd_rn(fym, 12582912.0f);
-  const uint32_t kx = (uint32_t)(__float_as_int(gx) - 0x4B400000), ky = (uint32_t)(__float_as_int(gy) - 0x4B400000);
+  const float gxx = __fadd_rn(fxm, 12582912.0f), gyy = __fadd_rn(fym, 12582912.0f);
+  const uint32_t kx = (uint32_t)(__float_as_int(gxx) - 0x4B400000), ky = (uint32_t)(__float_as_int(gyy) - 0x4B400000);
   // fm - k = fr - 1/2 (fr = fx - k), exact (k is an integer within 1/2 of fm, both below 2^22)
-  const float dx = __fsub_rn(fxm, __fsub_rn(gx, 12582912.0f)), dy = __fsub_rn(fym, __fsub_rn(gy, 12582912.0f));
-  // E + E' < 1/4, as hE + hE' > 3/4 (conservative by the extra 2^-20 in each hE)
-  const bool small_e = __fadd_rn(hEx, hEy) > 0.75f;
-  // E < fr < 1 - E for both axes: |fm - k| < hE < 1/2 - E
-  const bool ax_ok = (kx < (uint32_t)P.v.width) & (ky < (uint32_t)P.v.height) & (fabsf(dx) < hEx) & (fabsf(dy) < hEy);
-  // ---- state (the visible case first; the cull tests only where it fails)
+  const float dx = __fsub_rn(fxm, __fsub_rn(gxx, 12582912.0f)), dy = __fsub_rn(fym, __fsub_rn(gyy, 12582912.0f));
+  // E < fr < 1 - E for both axes: |fm - k| < hE < 1/2 - E (hE > 0 also bounds b below 1 / (2M + 1), which the
+  // bound E assumes)
+  const bool ax_ok = (kx < (uint32_t)P.v.width) & (ky < (uint32_t)P.v.height) & (fabsf(dx) < hE) & (fabsf(dy) < hE);
   uint32_t st;
-  if (in_range & depth_in & small_e & ax_ok & (exact | amb_ok)) {
+  if (in_range & depth_in & ax_ok & (exact | amb_ok)) {
     st = exact ? kExact : kAmbiguous;
   } else {
-    // Upper bounds of E: 1/2 - hE, rounded up (>= E + 2^-20 - 2^-25).
-    const float Ex = __fadd_ru(0.5f, -hEx), Ey = __fadd_ru(0.5f, -hEy);
-    // The bound E holds at any size (rho enters linearly; nothing assumes it small) while the values stay
-    // finite and w - dw > 0 (depth_in). Ex + Ey < 1e30 keeps E finite and, as Ex >= 5.65u W |ndx|, fx and fy
-    // below ~1.5e36: so a point far outside the image is culled here even where E is large (a point just
-    // in front of the camera and far to the side), instead of going to tier 2.
-    const bool finite_e = __fadd_rn(Ex, Ey) < 1e30f;
-    // fx_FP64 < 0 when fm + 1/2 + E < 0; fx_FP64 >= W when fm + 1/2 - E >= W (directed roundings)
-    const bool ax_out = (fxm < -__fadd_ru(0.5f, Ex)) | (fxm >= __fadd_ru(P.wm, Ex)) | (fym < -__fadd_ru(0.5f, Ey)) |
-                        (fym >= __fadd_ru(P.hm, Ey));
-    st = in_range & (depth_out | (depth_in & finite_e & ax_out)) ? kCulled : kDefer;
+    // Certainly culled? By depth: w_d <= wf + Delta < near, or w_d >= wf - Delta >= far (directed roundings).
+    const float dw = __fmaf_rn(P.kw, s, P.kw3);
+    const bool depth_out = (__fadd_ru(w, dw) < P.near_o) | (__fsub_rd(w, dw) >= P.far_o);
+    // By the pixel, for a point inside the depth window (wf > 0): b, g from the magnitude sums, and the bound
+    // E <= |fm| (9.8u + 1.35 b) + 1.35 g + ce, valid at any |fm| while b <= 1/4.
+    const float bf = __fmul_rn(__fmul_rn(__fmaf_rn(P.Mw, s, P.Mw3), r), P.cb);
+    const float gf = __fmul_rn(__fmul_rn(__fmaf_rn(P.MH, s, P.MH3), r), P.cb);
+    const float ea = __fmaf_rn(1.35f, bf, 9.8f * 0x1p-24f), eb = __fmaf_rn(1.35f, gf, P.ce);
+    const float ex = __fmaf_rn(fabsf(fxm), ea, eb), ey = __fmaf_rn(fabsf(fym), ea, eb);
+    // fx_d < 0 when fm + 1/2 + E < 0; fx_d >= W when fm + 1/2 - E >= W (for finite bounds: an overflow leaves
+    // the point to tier 2)
+    const bool ax_out = (fxm < -__fadd_ru(0.5f, ex)) | (fxm >= __fadd_ru(P.wm, ex)) | (fym < -__fadd_ru(0.5f, ey)) |
+                        (fym >= __fadd_ru(P.hm, ey));
+    const bool e_finite = __fadd_rn(ex, ey) < 3.0e38f;
+    st = in_range & (depth_out | (depth_in & (bf <= 0.25f) & e_finite & ax_out)) ? kCulled : kDefer;
   }
   out.state = st;
   out.pixel = ky * (uint32_t)P.v.width + kx;
@@ -693,8 +738,8 @@ __global__ void k_wait_check(uint32_t* __restrict__ status, uint32_t limit) {
 // Runs body(p0, valid0, p1, valid1) on every tile of the warp: the lane's two points of the tile; all 32
 // lanes call body together (body may use warp collectives). Returns false when a bounded wait gave up.
 template <typename Body>
-__device__ __forceinline__ bool stream_tiles(const uint4* __restrict__ pts, uint64_t n, uint4 (*ring)[kTile],
-                                             uint64_t* bar, uint32_t lane, Body&& body) {
+__device__ __forceinline__ bool stream_ring(const uint4* __restrict__ pts, uint64_t n, uint4 (*ring)[kTile],
+                                            uint64_t* bar, uint32_t lane, Body&& body) {
   const uint64_t n_tiles = (n + kTile - 1) / kTile;
   const uint64_t G = (uint64_t)gridDim.x * kCertWarps;
   const uint64_t g = (uint64_t)blockIdx.x * kCertWarps + (threadIdx.x >> 5);
@@ -723,6 +768,56 @@ __device__ __forceinline__ bool stream_tiles(const uint4* __restrict__ pts, uint
     body(p0, lane < cnt, p1, lane + 32u < cnt);
   }
   return true;
+}
+
+// The same tiles in the same order, loaded by the warp itself (16-byte loads, not allocated in L1), one tile
+// ahead: the two points of the warp's next tile are requested before the current tile is classified, so their
+// memory latency overlaps the classification. Full tiles take no bounds checks; the partial last tile (if any)
+// goes to the warp whose turn it is. No waits: always returns true. Measured on the 100M-point LIDAR frame it
+// issues fewer instructions per point than the ring (no barrier, copy or phase bookkeeping per tile) and runs
+// pass 1 in 0.58 ms against 0.71 ms.
+template <typename Body>
+__device__ __forceinline__ bool stream_direct(const uint4* __restrict__ pts, uint64_t n, uint32_t lane, Body&& body) {
+  const uint64_t n_full = n / kTile;
+  const uint64_t G = (uint64_t)gridDim.x * kCertWarps;
+  uint64_t t = (uint64_t)blockIdx.x * kCertWarps + (threadIdx.x >> 5);
+  const uint4* p = pts + t * kTile + lane;
+  const uint64_t step = G * kTile;
+  uint4 a0 = make_uint4(0u, 0u, 0u, 0u), a1 = a0;
+  if (t < n_full) {
+    a0 = ld_stream16(p);
+    a1 = ld_stream16(p + 32);
+  }
+#pragma unroll 1
+  for (; t < n_full; t += G) {
+    const uint4 c0 = a0, c1 = a1;
+    if (t + G < n_full) {
+      p += step;
+      a0 = ld_stream16(p);
+      a1 = ld_stream16(p + 32);
+    }
+    body(c0, true, c1, true);
+  }
+  const uint32_t rem = (uint32_t)(n - n_full * kTile);
+  if (t == n_full && rem != 0u) {
+    const uint4* b = pts + n_full * kTile;
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    const uint4 c0 = lane < rem ? ld_stream16(b + lane) : z;
+    const uint4 c1 = lane + 32u < rem ? ld_stream16(b + lane + 32) : z;
+    body(c0, lane < rem, c1, lane + 32u < rem);
+  }
+  return true;
+}
+
+// Point staging of the certified passes: kRing selects the bulk-copy rings (stream_ring), else direct loads
+// (stream_direct). A tuning choice (pcr_tuning.staging); both give the same results.
+template <bool kRing, typename Body>
+__device__ __forceinline__ bool stream_tiles(const uint4* __restrict__ pts, uint64_t n, uint4 (*ring)[kTile],
+                                             uint64_t* bar, uint32_t lane, Body&& body) {
+  if constexpr (kRing)
+    return stream_ring(pts, n, ring, bar, lane, body);
+  else
+    return stream_direct(pts, n, lane, body);
 }
 
 // Pass-1 handling of a tier-2 result: returns true when the point still has to go to the FP64 arbiter.
@@ -801,7 +896,7 @@ __device__ __forceinline__ void defer_points(bool defer, const uint4& p, uint4* 
 // Pass 1 (Section 2.1) with the certified transform. Tier 1 handles nearly every point; the others are
 // queued per warp in shared memory and handled 32 at a time by tier 2 and the FP64 arbiter. The points
 // arrive through the warp's bulk-copy ring (stream_tiles).
-template <bool kApprox, bool kMerge, bool kStats>
+template <bool kApprox, bool kMerge, bool kStats, bool kRing>
 __global__ void __launch_bounds__(kCertThreads, kApprox ? PCR_CERT_APPROX_MIN_BLOCKS : PCR_CERT_MIN_BLOCKS) k_raster_cert(
     const uint4* __restrict__ pts, uint64_t n, const __grid_constant__ CertParams P,
     unsigned long long* __restrict__ keys, unsigned long long* __restrict__ stats, uint32_t* __restrict__ status,
@@ -811,7 +906,7 @@ __global__ void __launch_bounds__(kCertThreads, kApprox ? PCR_CERT_APPROX_MIN_BL
   __shared__ __align__(128) uint4 ring[kCertWarps][2][kTile];
   __shared__ __align__(8) uint64_t bars[kCertWarps][2];
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-  if (lane == 0) ring_init(bars[warp]);
+  if (kRing && lane == 0) ring_init(bars[warp]);
   __syncwarp();
   if (!kApprox) load_table(P, table, sF);
   uint4* q = queue[warp];
@@ -852,7 +947,7 @@ __global__ void __launch_bounds__(kCertThreads, kApprox ? PCR_CERT_APPROX_MIN_BL
     if (!kApprox)
       defer_points(defer, p, q, qn, lane, [&](const uint4& d) { raster_deferred(P, sF, d, keys, &c_fp64); });
   };
-  const bool done = stream_tiles(pts, n, ring[warp], bars[warp], lane,
+  const bool done = stream_tiles<kRing>(pts, n, ring[warp], bars[warp], lane,
                                  [&](const uint4& p0, bool v0, const uint4& p1, bool v1) {
                                    point(p0, v0);
                                    point(p1, v1);
@@ -933,7 +1028,7 @@ __device__ __noinline__ void hq_deferred(const CertParams& P, const long long* s
 #ifndef PCR_HQ_MIN_BLOCKS
 #define PCR_HQ_MIN_BLOCKS 5
 #endif
-template <bool kApprox, bool kMerge>
+template <bool kApprox, bool kMerge, bool kRing>
 __global__ void __launch_bounds__(kCertThreads, PCR_HQ_MIN_BLOCKS) k_hq_cert(
     const uint4* __restrict__ pts, uint64_t n, const __grid_constant__ CertParams P,
     const unsigned long long* __restrict__ keys, unsigned long long* __restrict__ accum, uint32_t eps_num,
@@ -943,7 +1038,7 @@ __global__ void __launch_bounds__(kCertThreads, PCR_HQ_MIN_BLOCKS) k_hq_cert(
   __shared__ __align__(128) uint4 ring[kCertWarps][2][kTile];
   __shared__ __align__(8) uint64_t bars[kCertWarps][2];
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-  if (lane == 0) ring_init(bars[warp]);
+  if (kRing && lane == 0) ring_init(bars[warp]);
   __syncwarp();
   if (!kApprox) load_table(P, table, sF);
   uint4* q = queue[warp];
@@ -982,7 +1077,7 @@ __global__ void __launch_bounds__(kCertThreads, PCR_HQ_MIN_BLOCKS) k_hq_cert(
       defer_points(defer, p, q, qn, lane,
                    [&](const uint4& d) { hq_deferred(P, sF, d, keys, accum, eps_num, eps_den); });
   };
-  const bool done = stream_tiles(pts, n, ring[warp], bars[warp], lane,
+  const bool done = stream_tiles<kRing>(pts, n, ring[warp], bars[warp], lane,
                                  [&](const uint4& p0, bool v0, const uint4& p1, bool v1) {
                                    point(p0, v0);
                                    point(p1, v1);
@@ -993,10 +1088,12 @@ __global__ void __launch_bounds__(kCertThreads, PCR_HQ_MIN_BLOCKS) k_hq_cert(
 
 // ---------------------------------------------------------------------------------------------- launch
 
-// Launch tuning (per framebuffer, see pcr_set_tuning): same-pixel merging within a warp, grid size.
+// Launch tuning (per framebuffer, see pcr_set_tuning): same-pixel merging within a warp, grid size, point
+// staging (0: direct loads, 1: bulk-copy rings).
 struct Tuning {
   int merge = 0;
   int blocks_per_sm = 8;
+  int staging = 0;
 };
 
 inline unsigned cert_grid(uint64_t n, int sms, int per_sm) {
@@ -1021,23 +1118,26 @@ inline unsigned persistent_grid(int resident, uint64_t n, int sms, int per_sm) {
 }
 
 // table: device copy of P.F (or null: the kernels read it from the parameter block).
-template <bool kApprox, bool kMerge, bool kStats>
-inline void raster_launch3(const uint4* pts, uint64_t n, const CertParams& P, unsigned long long* keys,
+template <bool kApprox, bool kMerge, bool kStats, bool kRing>
+inline void raster_launch4(const uint4* pts, uint64_t n, const CertParams& P, unsigned long long* keys,
                            unsigned long long* stats, uint32_t* status, int sms, int per_sm, cudaStream_t s,
                            const long long* table) {
-  static const int resident = resident_blocks(k_raster_cert<kApprox, kMerge, kStats>);  // one per instantiation
+  static const int resident = resident_blocks(k_raster_cert<kApprox, kMerge, kStats, kRing>);  // per instantiation
   const unsigned grid = persistent_grid(resident, n, sms, per_sm);
-  k_raster_cert<kApprox, kMerge, kStats><<<grid, kCertThreads, 0, s>>>(pts, n, P, keys, stats, status, table);
+  k_raster_cert<kApprox, kMerge, kStats, kRing><<<grid, kCertThreads, 0, s>>>(pts, n, P, keys, stats, status, table);
 }
 
+// Pass 1 with the tuning's staging; the tier counters (stats) only with the exact transform, no merging.
 template <bool kApprox, bool kMerge>
 inline void raster_launch(const uint4* pts, uint64_t n, const CertParams& P, unsigned long long* keys,
                           unsigned long long* stats, uint32_t* status, int sms, int per_sm, cudaStream_t s,
-                          const long long* table = nullptr) {
+                          const long long* table = nullptr, int staging = 0) {
   if (stats && !kApprox && !kMerge)
-    raster_launch3<false, false, true>(pts, n, P, keys, stats, status, sms, per_sm, s, table);
+    staging ? raster_launch4<false, false, true, true>(pts, n, P, keys, stats, status, sms, per_sm, s, table)
+            : raster_launch4<false, false, true, false>(pts, n, P, keys, stats, status, sms, per_sm, s, table);
   else
-    raster_launch3<kApprox, kMerge, false>(pts, n, P, keys, nullptr, status, sms, per_sm, s, table);
+    staging ? raster_launch4<kApprox, kMerge, false, true>(pts, n, P, keys, nullptr, status, sms, per_sm, s, table)
+            : raster_launch4<kApprox, kMerge, false, false>(pts, n, P, keys, nullptr, status, sms, per_sm, s, table);
 }
 
 // The certified constants of a view, prepared on this thread and kept for the next call with the same view
@@ -1068,23 +1168,32 @@ inline bool launch_raster_certified(const uint4* pts, uint64_t n, const DevView&
     k_raster_fp64<<<grid, 256, 0, s>>>(pts, n, v, keys);
     return true;
   }
-  const int b = t.blocks_per_sm;
+  const int b = t.blocks_per_sm, g = t.staging;
   if (approximate)
-    t.merge ? raster_launch<true, true>(pts, n, *Pp, keys, stats, status, sms, b, s, table)
-            : raster_launch<true, false>(pts, n, *Pp, keys, stats, status, sms, b, s, table);
+    t.merge ? raster_launch<true, true>(pts, n, *Pp, keys, stats, status, sms, b, s, table, g)
+            : raster_launch<true, false>(pts, n, *Pp, keys, stats, status, sms, b, s, table, g);
   else
-    t.merge ? raster_launch<false, true>(pts, n, *Pp, keys, stats, status, sms, b, s, table)
-            : raster_launch<false, false>(pts, n, *Pp, keys, stats, status, sms, b, s, table);
+    t.merge ? raster_launch<false, true>(pts, n, *Pp, keys, stats, status, sms, b, s, table, g)
+            : raster_launch<false, false>(pts, n, *Pp, keys, stats, status, sms, b, s, table, g);
   return true;
+}
+
+template <bool kApprox, bool kMerge, bool kRing>
+inline void hq_launch3(const uint4* pts, uint64_t n, const CertParams& P, const unsigned long long* keys,
+                       unsigned long long* accum, uint32_t eps_num, uint32_t eps_den, uint32_t* status, int sms,
+                       int per_sm, cudaStream_t s, const long long* table) {
+  static const int resident = resident_blocks(k_hq_cert<kApprox, kMerge, kRing>);  // one per instantiation
+  const unsigned grid = persistent_grid(resident, n, sms, per_sm);
+  k_hq_cert<kApprox, kMerge, kRing><<<grid, kCertThreads, 0, s>>>(pts, n, P, keys, accum, eps_num, eps_den, status,
+                                                                  table);
 }
 
 template <bool kApprox, bool kMerge>
 inline void hq_launch(const uint4* pts, uint64_t n, const CertParams& P, const unsigned long long* keys,
                       unsigned long long* accum, uint32_t eps_num, uint32_t eps_den, uint32_t* status, int sms,
-                      int per_sm, cudaStream_t s, const long long* table = nullptr) {
-  static const int resident = resident_blocks(k_hq_cert<kApprox, kMerge>);  // one per instantiation
-  const unsigned grid = persistent_grid(resident, n, sms, per_sm);
-  k_hq_cert<kApprox, kMerge><<<grid, kCertThreads, 0, s>>>(pts, n, P, keys, accum, eps_num, eps_den, status, table);
+                      int per_sm, cudaStream_t s, const long long* table = nullptr, int staging = 0) {
+  staging ? hq_launch3<kApprox, kMerge, true>(pts, n, P, keys, accum, eps_num, eps_den, status, sms, per_sm, s, table)
+          : hq_launch3<kApprox, kMerge, false>(pts, n, P, keys, accum, eps_num, eps_den, status, sms, per_sm, s, table);
 }
 
 // Pass 2 for a view with n >= 1 points. status: the framebuffer's status word (timeout bit).
@@ -1098,13 +1207,13 @@ inline bool launch_hq_certified(const uint4* pts, uint64_t n, const DevView& v, 
     k_hq_fp64<<<grid, 256, 0, s>>>(pts, n, v, keys, accum, eps_num, eps_den);
     return true;
   }
-  const int b = t.blocks_per_sm;
+  const int b = t.blocks_per_sm, g = t.staging;
   if (approximate)
-    t.merge ? hq_launch<true, true>(pts, n, *Pp, keys, accum, eps_num, eps_den, status, sms, b, s, table)
-            : hq_launch<true, false>(pts, n, *Pp, keys, accum, eps_num, eps_den, status, sms, b, s, table);
+    t.merge ? hq_launch<true, true>(pts, n, *Pp, keys, accum, eps_num, eps_den, status, sms, b, s, table, g)
+            : hq_launch<true, false>(pts, n, *Pp, keys, accum, eps_num, eps_den, status, sms, b, s, table, g);
   else
-    t.merge ? hq_launch<false, true>(pts, n, *Pp, keys, accum, eps_num, eps_den, status, sms, b, s, table)
-            : hq_launch<false, false>(pts, n, *Pp, keys, accum, eps_num, eps_den, status, sms, b, s, table);
+    t.merge ? hq_launch<false, true>(pts, n, *Pp, keys, accum, eps_num, eps_den, status, sms, b, s, table, g)
+            : hq_launch<false, false>(pts, n, *Pp, keys, accum, eps_num, eps_den, status, sms, b, s, table, g);
   return true;
 }
 

@@ -38,7 +38,7 @@ class pcr_view(ctypes.Structure):
 
 
 class pcr_tuning(ctypes.Structure):
-    _fields_ = [("merge_same_pixel", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+    _fields_ = [("merge_same_pixel", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("staging", ctypes.c_int32)]
 
 
 class pcr_server_config(ctypes.Structure):
@@ -221,19 +221,23 @@ def pcr_framebuffer_info(fb: Framebuffer):
     return w.value, h.value, f.value
 
 
-def pcr_set_tuning(fb: Framebuffer, merge_same_pixel: int | None = 0, blocks_per_sm: int = 8):
+def _tuning_dict(t: pcr_tuning) -> dict:
+    return {"merge_same_pixel": t.merge_same_pixel, "blocks_per_sm": t.blocks_per_sm, "staging": t.staging}
+
+
+def pcr_set_tuning(fb: Framebuffer, merge_same_pixel: int | None = 0, blocks_per_sm: int = 8, staging: int = 0):
     """merge_same_pixel=None restores the library defaults."""
     if merge_same_pixel is None:
         _check(load().pcr_set_tuning(fb.handle, None))
     else:
-        t = pcr_tuning(int(merge_same_pixel), int(blocks_per_sm))
+        t = pcr_tuning(int(merge_same_pixel), int(blocks_per_sm), int(staging))
         _check(load().pcr_set_tuning(fb.handle, ctypes.byref(t)))
 
 
 def pcr_get_tuning(fb: Framebuffer):
     t = pcr_tuning()
     _check(load().pcr_get_tuning(fb.handle, ctypes.byref(t)))
-    return {"merge_same_pixel": t.merge_same_pixel, "blocks_per_sm": t.blocks_per_sm}
+    return _tuning_dict(t)
 
 
 def pcr_autotune(fb: Framebuffer, points, view, stream=None):
@@ -242,7 +246,7 @@ def pcr_autotune(fb: Framebuffer, points, view, stream=None):
     v = make_view(view)
     t = pcr_tuning()
     _check(load().pcr_autotune(fb.handle, ptr, n, ctypes.byref(v), _stream(stream), ctypes.byref(t)))
-    return {"merge_same_pixel": t.merge_same_pixel, "blocks_per_sm": t.blocks_per_sm}
+    return _tuning_dict(t)
 
 
 def pcr_clear(fb: Framebuffer, stream=None):

@@ -65,3 +65,36 @@ def test_replays_do_the_passes_framebuffer_work(gpu, ceil):
     o_pix, _, o_key = oracle.project(pts, view)
     assert np.array_equal(pix.cpu().numpy().astype(np.int64), o_pix)
     assert np.array_equal(key.cpu().numpy().view(np.uint64), o_key)
+
+
+def test_fma_probe_counts_and_rates(gpu, ceil):
+    """The FMA probe reports the fmas it enqueued (grid x threads x 8 chains x iters) and runs them: the
+    kernel time grows with iters, and the FP32 pipes outrun the FP64 pipe."""
+    import torch
+    vp = ctypes.c_void_p
+    ceil.pcr_ceiling_fma.argtypes = [ctypes.c_int32, ctypes.c_uint32, vp, ctypes.POINTER(ctypes.c_uint64), vp]
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    sink = torch.zeros(sms * 8 * 256, dtype=torch.int32, device="cuda")
+    s = torch.cuda.current_stream()
+    fmas = ctypes.c_uint64()
+    assert ceil.pcr_ceiling_fma(2, 10, vp(sink.data_ptr()), ctypes.byref(fmas), vp(s.cuda_stream)) != 0
+    assert ceil.pcr_ceiling_fma(1, 0, vp(sink.data_ptr()), ctypes.byref(fmas), vp(s.cuda_stream)) != 0
+
+    def rate(fp64, iters):
+        best = 1e30
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            assert ceil.pcr_ceiling_fma(fp64, iters, vp(sink.data_ptr()), ctypes.byref(fmas), vp(s.cuda_stream)) == 0
+            b.record(s)
+            b.synchronize()
+            best = min(best, a.elapsed_time(b))
+        assert fmas.value == sms * 8 * 256 * 8 * iters
+        return fmas.value / (best * 1e-3), best
+
+    r64, t_short = rate(1, 500)
+    r64b, t_long = rate(1, 2000)
+    r32, _ = rate(0, 50000)
+    assert t_long > 2.5 * t_short
+    assert r32 > 4 * r64b > 0
+    assert int(sink.sum().item()) == 0

@@ -281,14 +281,15 @@ def test_points_around_the_camera(gpu):
     assert tier2 < 0.005 * n
 
 
-@pytest.mark.parametrize("merge,blocks", [(0, 8), (1, 8), (1, 1), (1, 3), (0, 32)])
-def test_tuning_does_not_change_results(gpu, merge, blocks):
+@pytest.mark.parametrize("merge,blocks,staging", [(0, 8, 0), (1, 8, 0), (1, 1, 0), (1, 3, 0), (0, 32, 0), (0, 8, 1),
+                                                  (1, 8, 1), (1, 2, 1)])
+def test_tuning_does_not_change_results(gpu, merge, blocks, staging):
     import torch
     pts = scenes.lidar(2_000_003, 12)
     view = scenes.lidar_1km_view(800, 450)
     fb = gpu.pcr_create_framebuffer(view.width, view.height, gpu.PCR_FB_HQ)
-    gpu.pcr_set_tuning(fb, merge, blocks)
-    assert gpu.pcr_get_tuning(fb) == {"merge_same_pixel": merge, "blocks_per_sm": blocks}
+    gpu.pcr_set_tuning(fb, merge, blocks, staging)
+    assert gpu.pcr_get_tuning(fb) == {"merge_same_pixel": merge, "blocks_per_sm": blocks, "staging": staging}
     gpu.pcr_render_hq_splat(fb, _dev(pts), view)
     keys, acc = gpu.pcr_framebuffer_keys(fb)
     ref = oracle.render_atomicmin(pts, view)
@@ -300,3 +301,5 @@ def test_tuning_does_not_change_results(gpu, merge, blocks):
         gpu.pcr_set_tuning(fb, 2, 8)
     with pytest.raises(gpu.PcrError):
         gpu.pcr_set_tuning(fb, 1, 0)
+    with pytest.raises(gpu.PcrError):
+        gpu.pcr_set_tuning(fb, 0, 8, 2)

@@ -3,11 +3,12 @@ restated step by step in IEEE float32 (numpy rounds every float32 operation to n
 __fadd_rn / __fsub_rn / __fmaf_rn do; a directed rounding is restated with nextafter).
 
 Pixel axis. The kernel holds fm, a float estimate of fx - 1/2 for the definition's pixel coordinate fx, and
-hE < 1/2 - E, E a bound on |fx - (fm + 1/2)|. It floors without a conversion instruction: g = fm + 1.5 * 2^23
-rounds fm to the nearest integer k because the sum lies in [2^23, 2^24), where floats are the integers; k is
-the difference of the bit patterns of g and 1.5 * 2^23. The axis is decided when k < size and |fm - k| < hE:
-every fx within E of fm + 1/2 must then floor to k. It is certainly outside when fm < -RU(1/2 + E) or
-fm >= RU(size - 1/2 + E), E taken as RU(1/2 - hE).
+hE < 1/2 - E, E a bound on |fx - (fm + 1/2)| for a point inside the image. It floors without a conversion
+instruction: g = fm + 1.5 * 2^23 rounds fm to the nearest integer k because the sum lies in [2^23, 2^24), where
+floats are the integers; k is the difference of the bit patterns of g and 1.5 * 2^23. The axis is decided when
+k < size and |fm - k| < hE: every fx within E of fm + 1/2 must then floor to k. A point the kernel does not
+decide is certainly outside when fm < -RU(1/2 + Eg) or fm >= RU(size - 1/2 + Eg), Eg the kernel's bound of E
+that holds at any |fm|.
 
 Depth code. frac is the fixed-point fraction of t truncated to 23 bits; the code is certain when every t
 within D of the fixed-point value has the same floor. The kernel tests |frac - 1/2| < hD with
@@ -25,33 +26,37 @@ def _ru(a):
     return f if np.float64(f) >= a else np.nextafter(f, F32(np.inf))
 
 
-def pixel_axis(fm, hE, size):
-    """float32 restatement: returns (state, k); state 0 decided, 1 outside, 2 undecided."""
+def pixel_axis(fm, hE, size, eg=None):
+    """float32 restatement: returns (state, k); state 0 decided, 1 outside, 2 undecided. eg: the bound used for
+    the outside test (default: the largest bound a decided point may have, 1/2 - hE)."""
     fm, hE, size = F32(fm), F32(hE), np.uint32(size)
     with np.errstate(all="ignore"):
+        if eg is None:
+            eg = _ru(0.5 - np.float64(hE)) if np.isfinite(hE) else F32(np.nan)
+        eg = F32(eg)
         g = F32(fm + MAGIC)
         k = np.uint32((int(np.array(g, np.float32).view(np.int32)) - 0x4B400000) & 0xFFFFFFFF)
         d = F32(fm - F32(g - MAGIC))
         if k < size and abs(d) < hE:
             return 0, int(k)
-        Ex = _ru(0.5 - np.float64(hE)) if np.isfinite(hE) else F32(np.nan)
-        left = _ru(0.5 + np.float64(Ex))
-        right = _ru(np.float64(size) - 0.5 + np.float64(Ex))
-        if fm < -left or fm >= right:
+        left = _ru(0.5 + np.float64(eg))
+        right = _ru(np.float64(F32(np.float64(size) - 0.5)) + np.float64(eg))
+        if (fm < -left or fm >= right) and F32(eg + eg) < F32(3.0e38):  # a finite bound only
             return 1, None
     return 2, None
 
 
-def _check(values, hE, size):
+def _check(values, hE, size, eg=None):
     for fm in values:
-        st, k = pixel_axis(fm, hE, size)
+        st, k = pixel_axis(fm, hE, size, eg)
         f = np.float64(F32(fm)) + 0.5
         E = 0.5 - np.float64(F32(hE))  # the largest bound the kernel may have been given
         if st == 0:
             assert 0 <= k < size
             assert np.floor(f - E) == k and f + E < k + 1, (fm, k)
         elif st == 1:
-            assert f + E < 0 or f - E >= size, fm
+            Eo = E if eg is None else np.float64(F32(eg))
+            assert f + Eo < 0 or f - Eo >= size, fm
 
 
 def test_low_range_that_once_faulted():
@@ -79,9 +84,14 @@ def test_random_and_special_values():
     for hE in (0.5 - 2.0 ** -19, 0.49, 0.4, 0.1, 0.0, -5.0, -1e6, np.nan, -np.inf):
         _check(vals, hE, 16384)
     assert pixel_axis(np.nan, 0.49, 100)[0] == 2 and pixel_axis(1.5, np.nan, 100)[0] == 2
-    assert pixel_axis(np.inf, 0.49, 100)[0] == 1
+    assert pixel_axis(np.inf, 0.49, 100)[0] == 1 and pixel_axis(np.inf, 0.49, 100, np.inf)[0] == 2
     # a large bound still culls what is far enough outside, and decides nothing
     assert pixel_axis(-1e6, -100.0, 100)[0] == 1 and pixel_axis(50.0, -100.0, 100)[0] == 2
+    # the outside test with its own bound, as the kernel's cull branch takes it
+    for eg in (0.0, 2.0 ** -20, 1e-3, 0.3, 7.5, 1e6, np.inf, np.nan):
+        _check(vals, 0.49, 16384, eg)
+        _check(vals, -1.0, 1920, eg)
+    assert pixel_axis(-3e38, 0.49, 100, 1e30)[0] == 1
 
 
 def test_depth_fraction_test():
