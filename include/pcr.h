@@ -124,7 +124,7 @@ pcr_status pcr_set_tuning(pcr_framebuffer* fb, const pcr_tuning* tuning);
 pcr_status pcr_get_tuning(const pcr_framebuffer* fb, pcr_tuning* tuning);
 
 /* Autotuner: renders one frame of (d_points, n, view) on fb for every candidate tuning (same-pixel merging
- * on and off, 2 / 4 / 6 / 8 blocks per SM), times the point passes with CUDA events on `stream` (pass 1,
+ * on and off, both stagings, 2 / 4 / 6 / 8 blocks per SM), times the point passes with CUDA events on `stream` (pass 1,
  * plus pass 2 with eps 1/100 for HQ framebuffers; best of two runs), and keeps the fastest in fb. Writes it
  * to *best when best is not NULL. Clears fb before every run and at the end; synchronises `stream`.
  * Arguments as for pcr_render_atomicmin; n must be > 0. */
@@ -295,6 +295,39 @@ pcr_status pcr_batch_capture(pcr_batch* batch, pcr_stream_t stream);
 
 /* Launches the captured frame graph on `stream`. */
 pcr_status pcr_batch_launch(pcr_batch* batch, pcr_stream_t stream);
+
+/* Launch tuning of a batch's frames (the knobs of its autotuner). Results never depend on it. */
+typedef struct {
+  int32_t route;             /* 0 (default): automatic, single-view passes for frames of at most 4 views or clouds
+                                of at least 10^8 points (outside graph capture), else the batch kernel; 1: always
+                                the batch kernel; 2: always one single-view pass per view */
+  int32_t slice_words;       /* batch kernel work item: 1 (default), 2 or 4 words of a view's chunk mask
+                                (32, 64 or 128 chunks of 1024 points) */
+  int32_t points_per_thread; /* points a thread classifies per step of the batch kernel: 1 (default) or 2 */
+  int32_t blocks_per_sm;     /* 256-thread blocks per SM of the batch kernel, 1..32 (default 4; capped at the
+                                blocks that can be resident) */
+  int32_t merge_width;       /* 0 (default): one atomic per fragment; 8, 16 or 32: fragments of aligned groups of
+                                that many lanes that land on one pixel are merged first (warp match + reduction) */
+} pcr_batch_tuning;
+
+/* Sets the tuning used by the batch's later frames (NULL restores the defaults). A captured frame is
+ * re-captured by its next pcr_batch_launch (on that call's stream). */
+pcr_status pcr_batch_set_tuning(pcr_batch* batch, const pcr_batch_tuning* tuning);
+
+/* Current tuning of the batch. */
+pcr_status pcr_batch_get_tuning(const pcr_batch* batch, pcr_batch_tuning* tuning);
+
+/* Autotuner of the batched frame (the paper has no counterpart; its renderer has no tuning): renders the
+ * batch's frame (its cloud, views, mode) with candidate tunings on `stream`, times each with CUDA events (the
+ * best of two frames after one warm-up), and keeps the fastest in the batch. Candidates are explored one knob
+ * at a time from the automatic route's choice (route 1/2, slice_words, points_per_thread, blocks_per_sm,
+ * merge_width), keeping a change only when it is at least 2 % faster; two sweeps at most. The result is
+ * remembered for the process under the key (GPU name, mode, power-of-two buckets of the frame's pixels, views
+ * and points), and appended to the text file named by the environment variable PCR_AUTOTUNE_CACHE when it is
+ * set; with force = 0 a remembered result for the key (from the process or that file) is applied without
+ * timing anything. The frames rendered while tuning write the batch's framebuffers and images (as a render
+ * would). Synchronises `stream`. Writes the chosen tuning to *best when best is not NULL. Needs the views set. */
+pcr_status pcr_batch_autotune(pcr_batch* batch, pcr_stream_t stream, int32_t force, pcr_batch_tuning* best);
 
 /* Visible-chunk counts of the last frame per view (host array of count entries; synchronises the
  * device). A diagnostic of the culling. */

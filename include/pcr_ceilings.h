@@ -50,7 +50,7 @@ int pcr_ceiling_pattern_hq(const uint32_t* d_pix, const uint64_t* d_key, uint64_
                            uint64_t* d_accum, uint32_t eps_num, uint32_t eps_den, uint64_t nq, void* stream);
 
 /* Fused multiply-add throughput of the FP64 (fp64 = 1) or FP32 (fp64 = 0) pipes: sms * 8 blocks of 256
- * threads, each running 8 independent chains of `iters` explicitly rounded fmas. *fmas receives the total
+ * threads, each running 16 independent chains of `iters` explicitly rounded fmas. *fmas receives the total
  * number of fmas enqueued (host memory); divide by the kernel's time for the rate. The FP64 rate is what a
  * direct FP64 evaluation of the per-point transform (Sections 1 and 2.1: depth in double precision) is
  * bound by. d_sink must hold sms * 8 * 256 u32; iters >= 1. */

@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(256) k_pattern_hq(const uint32_t* __restrict__
 // Fused multiply-add throughput: every thread runs kFmaChains independent chains of `iters` fmas each
 // (explicitly rounded, so nothing is contracted or folded), then writes to sink only when the sum hits an
 // impossible value. The chains hide the pipe latency at full occupancy.
-constexpr int kFmaChains = 8;
+constexpr int kFmaChains = 16;
 constexpr int kFmaThreads = 256;
 constexpr int kFmaBlocksPerSm = 8;
 

@@ -4,7 +4,9 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -315,27 +317,26 @@ pcr_status pcr_autotune(pcr_framebuffer* fb, const pcr_point* d_points, uint64_t
   pcr::Tuning best_t = saved;
   float best_ms = 3.0e38f;
   pcr_status st = PCR_OK;
-  for (int merge = 0; merge <= 1 && st == PCR_OK; ++merge) {
-    for (int b : {2, 4, 6, 8}) {
-      fb->tuning.merge = merge;
-      fb->tuning.blocks_per_sm = b;
-      float run_best = 3.0e38f;
-      for (int rep = 0; rep < 2 && st == PCR_OK; ++rep) {
-        if ((st = pcr_clear(fb, stream)) != PCR_OK) break;
-        cudaEventRecord(e0, s);
-        st = launch_raster(fb, d_points, n, dv, view->transform, s);
-        if (st == PCR_OK && hq) st = launch_hq(fb, d_points, n, dv, view->transform, 1, 100, s);
-        cudaEventRecord(e1, s);
-        if (cudaEventSynchronize(e1) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "autotune timing");
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        run_best = ms < run_best ? ms : run_best;
-      }
-      if (st != PCR_OK) break;
-      if (run_best < best_ms) {
-        best_ms = run_best;
-        best_t = fb->tuning;
-      }
+  for (int cand = 0; cand < 16 && st == PCR_OK; ++cand) {
+    fb->tuning.merge = cand & 1;
+    fb->tuning.staging = (cand >> 1) & 1;
+    fb->tuning.blocks_per_sm = 2 + 2 * (cand >> 2);  // 2, 4, 6, 8
+    float run_best = 3.0e38f;
+    for (int rep = 0; rep < 2 && st == PCR_OK; ++rep) {
+      if ((st = pcr_clear(fb, stream)) != PCR_OK) break;
+      cudaEventRecord(e0, s);
+      st = launch_raster(fb, d_points, n, dv, view->transform, s);
+      if (st == PCR_OK && hq) st = launch_hq(fb, d_points, n, dv, view->transform, 1, 100, s);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "autotune timing");
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      run_best = ms < run_best ? ms : run_best;
+    }
+    if (st != PCR_OK) break;
+    if (run_best < best_ms) {
+      best_ms = run_best;
+      best_t = fb->tuning;
     }
   }
   cudaEventDestroy(e0);

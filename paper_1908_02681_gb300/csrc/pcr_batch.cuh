@@ -10,9 +10,10 @@
 //     the near plane, beyond the far plane, or at |ndc| > 1 + 1e-5, which the definition's float pixel
 //     mapping (relative error below 1e-6) sends outside the image. A box with a NaN or infinite bound is
 //     never skipped.
-//   * one persistent launch per pass for all views: work items are (range of kSlice consecutive chunks,
-//     view), taken range by range from a counter, so a range is read from HBM once for all views; a block
-//     reloads a view's depth table when its view changes.
+//   * one persistent launch per pass for all views: work items are (range of consecutive chunks, view),
+//     taken range by range from a counter, so a range is read from HBM once for all views; a block
+//     reloads a view's depth table when its view changes. The range size, points per thread, grid size and
+//     same-pixel merging are launch tuning (BatchTuning), picked by an autotuner (pcr_batch_autotune).
 //   * one resolve launch for all views.
 #pragma once
 
@@ -21,7 +22,6 @@
 namespace pcr {
 
 constexpr int kChunk = 1024;        // points per chunk (bounding box granularity)
-constexpr int kSlice = 32;          // consecutive chunks per work item (one word of a view's mask)
 constexpr int kMaxBatchViews = 256;
 
 // Per-view constants of a batch that live in device memory (read once per work item).
@@ -136,30 +136,49 @@ __global__ void k_items(uint32_t* __restrict__ next_item) {
 
 // ------------------------------------------------------------------------------------------- batch passes
 
+constexpr int kMaxSliceWords = 4;  // largest work item: 4 mask words = 128 chunks
+
+// Launch tuning of a batched frame (pcr_batch_tuning in include/pcr.h). Results never depend on it.
+struct BatchTuning {
+  int route = 0;              // 0: automatic (per-view passes for few views or large clouds), 1: batch kernel,
+                              // 2: one single-view pass per view
+  int slice_words = 1;        // mask words (32 chunks each) per work item: 1, 2 or 4
+  int points_per_thread = 1;  // points a thread classifies per step: 1 or 2
+  int blocks_per_sm = 4;      // capped at the blocks that can be resident
+  int merge_width = 0;        // 0: one atomic per fragment; 8, 16 or 32: same-pixel fragments of that many
+                              // lanes merged first
+};
+
 // Pass 1 (kHq = false) or pass 2 (kHq = true) for every view of a batch, one persistent launch. Work item
-// = (range r of kSlice consecutive chunks, view v), numbered r * n_views + v and taken in that order from
-// next_item[kHq]: the views of one range run close together in time, so the range's points come from HBM
-// once and from L2 for the other views. An item covers the range's chunks whose mask bit is set.
-// params: per-view CertParams in device memory (tier 2 and the FP64 arbiter read them there; tier 1 holds
-// its constants in registers for the item).
-template <bool kHq>
+// = (range r of slice_words consecutive mask words, i.e. 32 * slice_words chunks, view v), numbered
+// r * n_views + v and taken in that order from next_item[kHq]: the views of one range run close together in
+// time, so the range's points come from HBM once and from L2 for the other views. Warp 0 lists the range's
+// chunks whose mask bit is set; the block then walks them in steps of kCertThreads * kPts points (each warp
+// takes 32 * kPts consecutive points per step), loading the next step's points before classifying the
+// current ones. params: per-view CertParams in device memory (tier 2 and the FP64 arbiter read them there;
+// tier 1 holds its constants in registers for the item). merge_width: see BatchTuning (kMerge = width > 0).
 #ifndef PCR_BATCH_MIN_BLOCKS
 #define PCR_BATCH_MIN_BLOCKS 4
 #endif
-__global__ void __launch_bounds__(kCertThreads, PCR_BATCH_MIN_BLOCKS) k_batch_pass(const uint4* __restrict__ pts, uint64_t n,
-                                                             const CertParams* __restrict__ params,
-                                                             const BatchSlot* __restrict__ slots,
-                                                             const uint32_t* __restrict__ masks, uint32_t n_views,
-                                                             uint32_t n_chunks, uint32_t* __restrict__ next_item,
-                                                             uint32_t eps_num, uint32_t eps_den) {
+template <bool kHq, bool kMerge, int kPts>
+__global__ void __launch_bounds__(kCertThreads, PCR_BATCH_MIN_BLOCKS) k_batch_pass(
+    const uint4* __restrict__ pts, uint64_t n, const CertParams* __restrict__ params,
+    const BatchSlot* __restrict__ slots, const uint32_t* __restrict__ masks, uint32_t n_views, uint32_t n_chunks,
+    uint32_t* __restrict__ next_item, uint32_t eps_num, uint32_t eps_den, uint32_t slice_words,
+    uint32_t merge_width) {
   __shared__ long long sF[3 * kTableEntries];
   __shared__ uint4 queue[kCertWarps][kQueue];
-  __shared__ uint32_t s_item;
+  __shared__ uint32_t s_chunks[kMaxSliceWords * 32];
+  __shared__ uint32_t s_item, s_nvis;
+  static_assert(kPts == 1 || kPts == 2, "one or two points per thread per step");
+  static_assert(kChunk % (kCertThreads * kPts) == 0, "whole steps per chunk");
+  constexpr uint32_t kSteps = kChunk / (kCertThreads * kPts);  // steps per chunk
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   uint4* q = queue[warp];
-  static_assert(kSlice == 32, "a range is one word of the view's mask");
   const uint32_t words = (n_chunks + 31u) / 32u;
-  const uint32_t total = (n_chunks + kSlice - 1) / kSlice * n_views;
+  const uint32_t ranges = (words + slice_words - 1u) / slice_words;
+  const uint32_t total = ranges * n_views;
+  const uint32_t seg = merge_segment(lane, merge_width);
   uint32_t cur_view = 0xFFFFFFFFu;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(next_item + (kHq ? 1 : 0), 1u);
@@ -167,12 +186,20 @@ __global__ void __launch_bounds__(kCertThreads, PCR_BATCH_MIN_BLOCKS) k_batch_pa
     const uint32_t item = s_item;
     if (item >= total) break;
     const uint32_t r = item / n_views, v = item - r * n_views;
-    const uint32_t c0 = r * kSlice;
-    const uint32_t bits = masks[(uint64_t)v * words + c0 / 32u];  // kSlice == 32: the whole word
-    if (bits == 0u) {  // nothing of this range is visible in this view (the same in every thread)
-      __syncthreads();
-      continue;
+    const uint32_t w0 = r * slice_words;
+    const uint32_t wn = words - w0 < slice_words ? words - w0 : slice_words;
+    if (warp == 0) {  // the visible chunks of the item, in increasing order
+      uint32_t cnt = 0;
+      for (uint32_t k = 0; k < wn; ++k) {
+        const uint32_t bits = masks[(uint64_t)v * words + w0 + k];
+        if ((bits >> lane) & 1u) s_chunks[cnt + __popc(bits & ((1u << lane) - 1u))] = (w0 + k) * 32u + lane;
+        cnt += __popc(bits);
+      }
+      if (lane == 0) s_nvis = cnt;
     }
+    __syncthreads();
+    const uint32_t nvis = s_nvis;
+    if (nvis == 0u) continue;  // nothing of this range is visible in this view (the same in every thread)
     if (v != cur_view) {
       const long long* src = &params[v].F[0][0];
       for (int i = threadIdx.x; i < 3 * kTableEntries; i += blockDim.x) sF[i] = src[i];
@@ -190,73 +217,71 @@ __global__ void __launch_bounds__(kCertThreads, PCR_BATCH_MIN_BLOCKS) k_batch_pa
     __builtin_assume(__isGlobal(keys));
     __builtin_assume(accum == nullptr || __isGlobal(accum));
     uint32_t qn = 0;
-    // the item's points as one sequence of steps (kChunk / kCertThreads per chunk); the point of the next
-    // step is loaded before the current one is classified, so its memory latency overlaps the work
-    static_assert(kChunk % kCertThreads == 0, "whole steps per chunk");
-    constexpr uint32_t kPerChunk = kChunk / kCertThreads;
-    const uint32_t steps = (uint32_t)__popc(bits) * kPerChunk;
-    // the chunk of the next step and its part: visible chunks in increasing order (lowest remaining bit)
-    uint32_t rem = bits & (bits - 1u), nc = c0 + (uint32_t)(__ffs(bits) - 1), nk = 0;
-    uint64_t i_next = (uint64_t)nc * kChunk + warp * 32u + lane;
-    uint4 p_next = i_next < n ? ld_stream16(pts + i_next) : make_uint4(0u, 0u, 0u, 0u);
+    const uint32_t steps = nvis * kSteps;
+    // first point of this warp in step st: chunk s_chunks[st / kSteps], part st % kSteps of it
+    auto first = [&](uint32_t st) -> uint64_t {
+      return (uint64_t)s_chunks[st / kSteps] * kChunk + (st % kSteps) * (kCertThreads * kPts) + warp * (32u * kPts) +
+             lane;
+    };
+    auto load = [&](uint64_t i) { return i < n ? ld_stream16(pts + i) : make_uint4(0u, 0u, 0u, 0u); };
+    // one point: tier 1, then the pass's commit, then the deferral of a point tier 1 could not decide
+    auto point = [&](const uint4& p, bool valid) {
+      bool defer = false;
+      if (!kHq) {
+        bool has = false;
+        uint32_t pix = 0;
+        unsigned long long key = 0;
+        if (valid) {
+          const FastFrag f = classify_fast(H, sF, p);
+          pix = f.pixel;
+          key = key_from_fixed(f.a0, f.a1, f.a2, p.w);
+          has = f.state == kExact;
+          defer = f.state == kDefer;
+          if (f.state == kAmbiguous) {
+            const unsigned long long klo = f.lo_half ? key - (1ull << 24) : key;
+            defer = klo < stored_key(keys, pix);
+          }
+        }
+        commit_min<kMerge>(has && key < stored_key(keys, pix), pix, key, keys, lane, seg);
+        unsigned dummy = 0;
+        defer_points(defer, p, q, qn, lane, [&](const uint4& d) { raster_deferred(Pg, sF, d, keys, &dummy); });
+      } else {
+        bool accept = false;
+        uint32_t pix = 0;
+        if (valid) {
+          const FastFrag f = classify_fast(H, sF, p);
+          pix = f.pixel;
+          defer = f.state == kDefer;
+          if ((f.state == kExact) | (f.state == kAmbiguous)) {
+            const unsigned long long qmin = stored_key(keys, pix) >> 24;
+            const unsigned long long qc = code_from_fixed(f.a1, f.a2);
+            const bool amb = f.state == kAmbiguous;
+            accept = in_band(amb && f.lo_half ? qc - 1 : qc, qmin, Pg.v.nq, eps_num, eps_den);
+            if (amb) {
+              const bool other = in_band(f.lo_half ? qc : qc + 1, qmin, Pg.v.nq, eps_num, eps_den);
+              defer = accept != other;
+              accept = accept && !defer;
+            }
+          }
+        }
+        commit_add<kMerge>(accept, pix, p.w, accum, lane, seg);
+        defer_points(defer, p, q, qn, lane,
+                     [&](const uint4& d) { hq_deferred(Pg, sF, d, keys, accum, eps_num, eps_den); });
+      }
+    };
+    uint64_t i_next = first(0);
+    uint4 a0 = load(i_next), a1 = kPts == 2 ? load(i_next + 32) : a0;
 #pragma unroll 1
     for (uint32_t st = 0; st < steps; ++st) {
-      {
-        const uint64_t i = i_next;
-        const bool valid = i < n;
-        const uint4 p = p_next;
-        if (st + 1 < steps) {
-          if (++nk == kPerChunk) {  // next visible chunk of the range (there is one: more steps remain)
-            nk = 0;
-            nc = c0 + (uint32_t)(__ffs(rem) - 1);
-            rem &= rem - 1u;
-          }
-          i_next = (uint64_t)nc * kChunk + nk * kCertThreads + warp * 32u + lane;
-          p_next = i_next < n ? ld_stream16(pts + i_next) : make_uint4(0u, 0u, 0u, 0u);
-        }
-        bool defer = false;
-        if (!kHq) {
-          bool has = false;
-          uint32_t pix = 0;
-          unsigned long long key = 0;
-          if (valid) {
-            const FastFrag f = classify_fast(H, sF, p);
-            pix = f.pixel;
-            key = key_from_fixed(f.a0, f.a1, f.a2, p.w);
-            has = f.state == kExact;
-            defer = f.state == kDefer;
-            if (f.state == kAmbiguous) {
-              const unsigned long long klo = f.lo_half ? key - (1ull << 24) : key;
-              defer = klo < keys[pix];
-            }
-          }
-          if (has && key < stored_key(keys, pix)) atomicMin(keys + pix, key);
-          unsigned dummy = 0;
-          defer_points(defer, p, q, qn, lane, [&](const uint4& d) { raster_deferred(Pg, sF, d, keys, &dummy); });
-        } else {
-          bool accept = false;
-          uint32_t pix = 0;
-          if (valid) {
-            const FastFrag f = classify_fast(H, sF, p);
-            pix = f.pixel;
-            defer = f.state == kDefer;
-            if (f.state == kExact || f.state == kAmbiguous) {
-              const unsigned long long qmin = keys[pix] >> 24;
-              const unsigned long long qc = code_from_fixed(f.a1, f.a2);
-              bool acc = in_band(f.state == kAmbiguous && f.lo_half ? qc - 1 : qc, qmin, Pg.v.nq, eps_num, eps_den);
-              if (f.state == kAmbiguous) {
-                const bool other = in_band(f.lo_half ? qc : qc + 1, qmin, Pg.v.nq, eps_num, eps_den);
-                defer = acc != other;
-                acc = acc && !defer;
-              }
-              accept = acc;
-            }
-          }
-          if (accept) hq_add(accum, pix, p.w);
-          defer_points(defer, p, q, qn, lane,
-                       [&](const uint4& d) { hq_deferred(Pg, sF, d, keys, accum, eps_num, eps_den); });
-        }
+      const uint64_t i = i_next;
+      const uint4 c0 = a0, c1 = a1;
+      if (st + 1 < steps) {  // the next step's points, requested before this step's are classified
+        i_next = first(st + 1);
+        a0 = load(i_next);
+        if (kPts == 2) a1 = load(i_next + 32);
       }
+      point(c0, i < n);
+      if (kPts == 2) point(c1, i + 32 < n);
     }
     // the queue holds points of this view only: finish them before the next item
     if (lane < qn) {
@@ -270,6 +295,46 @@ __global__ void __launch_bounds__(kCertThreads, PCR_BATCH_MIN_BLOCKS) k_batch_pa
     __syncwarp();
     __syncthreads();
   }
+}
+
+// Launches the batch pass kernel of a tuning (template instance by merging and points per thread).
+template <bool kHq>
+inline void batch_pass_launch(const BatchTuning& t, int sms, int resident, const uint4* pts, uint64_t n,
+                              const CertParams* params, const BatchSlot* slots, const uint32_t* masks,
+                              uint32_t n_views, uint32_t n_chunks, uint32_t* next_item, uint32_t eps_num,
+                              uint32_t eps_den, cudaStream_t s) {
+  const int per_sm = t.blocks_per_sm < resident ? t.blocks_per_sm : resident;
+  const unsigned grid = (unsigned)(sms * (per_sm > 0 ? per_sm : 1));
+  const uint32_t sw = (uint32_t)t.slice_words, mw = (uint32_t)t.merge_width;
+#define PCR_BATCH_LAUNCH(M, K)                                                                                    \
+  k_batch_pass<kHq, M, K><<<grid, kCertThreads, 0, s>>>(pts, n, params, slots, masks, n_views, n_chunks, next_item, \
+                                                        eps_num, eps_den, sw, mw)
+  if (t.merge_width > 0) {
+    if (t.points_per_thread == 2) PCR_BATCH_LAUNCH(true, 2); else PCR_BATCH_LAUNCH(true, 1);
+  } else {
+    if (t.points_per_thread == 2) PCR_BATCH_LAUNCH(false, 2); else PCR_BATCH_LAUNCH(false, 1);
+  }
+#undef PCR_BATCH_LAUNCH
+}
+
+// Resident blocks per SM of the batch pass kernel of a tuning.
+template <bool kHq>
+inline int batch_pass_resident(const BatchTuning& t) {
+  int b = 0;
+  cudaError_t e;
+  if (t.merge_width > 0)
+    e = t.points_per_thread == 2
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_pass<kHq, true, 2>, kCertThreads, 0)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_pass<kHq, true, 1>, kCertThreads, 0);
+  else
+    e = t.points_per_thread == 2
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_pass<kHq, false, 2>, kCertThreads, 0)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_pass<kHq, false, 1>, kCertThreads, 0);
+  if (e != cudaSuccess || b < 1) {
+    cudaGetLastError();
+    b = 1;
+  }
+  return b;
 }
 
 // Resolve of every framebuffer of a batch (pcr_resolve semantics per view), one launch. pixel_start[v] =

@@ -854,20 +854,25 @@ __device__ __forceinline__ unsigned long long stored_key(const unsigned long lon
   return __ldcg(keys + pix);
 }
 
-// Commits one key per lane (has = true) with one atomic minimum per distinct pixel of the warp: lanes
-// whose fragments land on the same pixel are grouped (match.any) and their smallest key found with two
-// 32-bit warp reductions (high word, then low word among the lanes holding the smallest high word).
-// All 32 lanes must call it.
+// Lanes a lane may merge with when merging is limited to aligned groups of `width` lanes (8, 16 or 32).
+__device__ __forceinline__ uint32_t merge_segment(uint32_t lane, uint32_t width) {
+  return width >= 32u ? 0xFFFFFFFFu : ((1u << width) - 1u) << (lane & ~(width - 1u));
+}
+
+// Commits one key per lane (has = true) with one atomic minimum per distinct pixel of each lane segment
+// (seg: merge_segment): lanes whose fragments land on the same pixel are grouped (match.any) and their
+// smallest key found with two 32-bit reductions (high word, then low word among the lanes holding the
+// smallest high word). All 32 lanes must call it.
 template <bool kMerge>
 __device__ __forceinline__ void commit_min(bool has, uint32_t pix, unsigned long long key, unsigned long long* keys,
-                                           uint32_t lane) {
+                                           uint32_t lane, uint32_t seg = 0xFFFFFFFFu) {
   if (!kMerge) {
     if (has) atomicMin(keys + pix, key);
     return;
   }
   const unsigned act = __ballot_sync(0xFFFFFFFFu, has);
   if (has) {
-    const unsigned grp = __match_any_sync(act, pix);
+    const unsigned grp = __match_any_sync(act, pix) & seg;
     const unsigned hi = (unsigned)(key >> 32), lo = (unsigned)key;
     const unsigned mhi = __reduce_min_sync(grp, hi);
     const unsigned mlo = __reduce_min_sync(grp, hi == mhi ? lo : 0xFFFFFFFFu);
@@ -986,18 +991,18 @@ __device__ __forceinline__ void hq_add(unsigned long long* accum, uint32_t pix, 
   atomicAdd(accum + 2 * (uint64_t)pix + 1, hq_bc(rgba));
 }
 
-// Adds the colours of the accepted fragments with one pair of atomics per distinct pixel of the warp
-// (per-channel warp sums: at most 32 * 255, no carry between the packed fields). All lanes must call it.
+// Adds the colours of the accepted fragments with one pair of atomics per distinct pixel of each lane segment
+// (per-channel sums: at most 32 * 255, no carry between the packed fields). All lanes must call it.
 template <bool kMerge>
 __device__ __forceinline__ void commit_add(bool add, uint32_t pix, uint32_t rgba, unsigned long long* accum,
-                                           uint32_t lane) {
+                                           uint32_t lane, uint32_t seg = 0xFFFFFFFFu) {
   if (!kMerge) {
     if (add) hq_add(accum, pix, rgba);
     return;
   }
   const unsigned act = __ballot_sync(0xFFFFFFFFu, add);
   if (add) {
-    const unsigned grp = __match_any_sync(act, pix);
+    const unsigned grp = __match_any_sync(act, pix) & seg;
     const unsigned r = __reduce_add_sync(grp, rgba & 0xFFu);
     const unsigned g = __reduce_add_sync(grp, (rgba >> 8) & 0xFFu);
     const unsigned b = __reduce_add_sync(grp, (rgba >> 16) & 0xFFu);

@@ -41,6 +41,11 @@ class pcr_tuning(ctypes.Structure):
     _fields_ = [("merge_same_pixel", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("staging", ctypes.c_int32)]
 
 
+class pcr_batch_tuning(ctypes.Structure):
+    _fields_ = [("route", ctypes.c_int32), ("slice_words", ctypes.c_int32), ("points_per_thread", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("merge_width", ctypes.c_int32)]
+
+
 class pcr_server_config(ctypes.Structure):
     _fields_ = [("streams", ctypes.c_int32), ("max_batch_views", ctypes.c_int32),
                 ("framebuffer_budget_bytes", ctypes.c_uint64), ("max_frame_point_views", ctypes.c_uint64)]
@@ -99,6 +104,9 @@ def _declare(lib):
         "pcr_batch_capture": ([_P, _P], S),
         "pcr_batch_launch": ([_P, _P], S),
         "pcr_batch_visible_chunks": ([_P, _P], S),
+        "pcr_batch_set_tuning": ([_P, ctypes.POINTER(pcr_batch_tuning)], S),
+        "pcr_batch_get_tuning": ([_P, ctypes.POINTER(pcr_batch_tuning)], S),
+        "pcr_batch_autotune": ([_P, _P, ctypes.c_int32, ctypes.POINTER(pcr_batch_tuning)], S),
         "pcr_batch_destroy": ([_P], S),
         "pcr_render_views_noalloc": ([_P, ctypes.c_uint64, _P, _P, _P, ctypes.c_int32, ctypes.c_int32,
                                       ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int32, _P], S),
@@ -458,6 +466,32 @@ def pcr_batch_visible_chunks(batch: Batch) -> list[int]:
     arr = (ctypes.c_uint32 * len(batch.fbs))()
     _check(load().pcr_batch_visible_chunks(batch.handle, arr))
     return list(arr)
+
+
+BATCH_TUNING_FIELDS = ("route", "slice_words", "points_per_thread", "blocks_per_sm", "merge_width")
+
+
+def pcr_batch_set_tuning(batch: Batch, tuning: dict | None = None):
+    """tuning: a dict with the pcr_batch_tuning fields (missing ones take the defaults); None restores them."""
+    if tuning is None:
+        _check(load().pcr_batch_set_tuning(batch.handle, None))
+        return
+    d = {"route": 0, "slice_words": 1, "points_per_thread": 1, "blocks_per_sm": 4, "merge_width": 0, **tuning}
+    t = pcr_batch_tuning(*[int(d[k]) for k in BATCH_TUNING_FIELDS])
+    _check(load().pcr_batch_set_tuning(batch.handle, ctypes.byref(t)))
+
+
+def pcr_batch_get_tuning(batch: Batch) -> dict:
+    t = pcr_batch_tuning()
+    _check(load().pcr_batch_get_tuning(batch.handle, ctypes.byref(t)))
+    return {k: getattr(t, k) for k in BATCH_TUNING_FIELDS}
+
+
+def pcr_batch_autotune(batch: Batch, stream=None, force: bool = False) -> dict:
+    """Times candidate tunings on the batch's frame and keeps the fastest; returns it."""
+    t = pcr_batch_tuning()
+    _check(load().pcr_batch_autotune(batch.handle, _stream(stream), int(bool(force)), ctypes.byref(t)))
+    return {k: getattr(t, k) for k in BATCH_TUNING_FIELDS}
 
 
 def pcr_batch_destroy(batch: Batch):

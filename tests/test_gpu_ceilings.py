@@ -68,7 +68,7 @@ def test_replays_do_the_passes_framebuffer_work(gpu, ceil):
 
 
 def test_fma_probe_counts_and_rates(gpu, ceil):
-    """The FMA probe reports the fmas it enqueued (grid x threads x 8 chains x iters) and runs them: the
+    """The FMA probe reports the fmas it enqueued (grid x threads x 16 chains x iters) and runs them: the
     kernel time grows with iters, and the FP32 pipes outrun the FP64 pipe."""
     import torch
     vp = ctypes.c_void_p
@@ -89,7 +89,7 @@ def test_fma_probe_counts_and_rates(gpu, ceil):
             b.record(s)
             b.synchronize()
             best = min(best, a.elapsed_time(b))
-        assert fmas.value == sms * 8 * 256 * 8 * iters
+        assert fmas.value == sms * 8 * 256 * 16 * iters
         return fmas.value / (best * 1e-3), best
 
     r64, t_short = rate(1, 500)

@@ -89,3 +89,21 @@ def test_noalloc_at_its_size_limits(gpu):
     torch.cuda.synchronize()
     for k, (a, b) in enumerate(zip(outs, want)):
         assert bool((a == b).all()), k
+
+
+def test_noalloc_call_allocates_no_device_memory(gpu):
+    """After a first call on the device (which looks up the array and loads the kernels), a call changes the
+    device's free memory by nothing: it allocates nothing."""
+    import torch
+    dev = _dev(scenes.lidar(500_003, 35))
+    views = scenes.orbit_views(4, 35, resolutions=RES)
+    fbs = [gpu.pcr_create_framebuffer(v.width, v.height, gpu.PCR_FB_HQ) for v in views]
+    outs = [torch.empty(v.width * v.height, dtype=torch.int32, device="cuda") for v in views]
+    for hq in (True, False):  # warm-up: both passes' kernels loaded
+        gpu.pcr_render_views_noalloc(dev, fbs, outs, views, hq=hq)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    gpu.pcr_render_views_noalloc(dev, fbs, outs, views, hq=True)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
