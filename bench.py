@@ -13,7 +13,12 @@ buildings, 1 cm noise, height-ramp RGB, coherent scan order), 1920x1080, fov 60,
 linear 40-bit depth, eps = 1 %. It stands in for the paper's scanned data sets (Table 1), which are not
 available. Inputs are 1.6 GB, larger than the 129 MB L2, so no L2 flush is needed between steps.
 
---impl reference times the oracle (single-threaded FP64 C++) on a bounded sample of the same workload.
+After the main timed region, one GPU also reports two sub-results (each timed on its own, not part of
+`value`): `batched`, 64 orbit views of a 20M-point cloud at mixed resolutions in one autotuned batched frame
+against the same views rendered one view per launch; and `serving`, a Poisson request stream over 6 resident
+clouds served with continuous batching (frames/s, p50/p99 latency) against one request per frame.
+
+--impl reference times the oracle (single-threaded FP64 C++) on the workload (or a bounded sample of it).
 Multi-GPU (torchrun): independent replicas, one full frame per rank per step (weak scaling).
 """
 from __future__ import annotations
@@ -381,8 +386,8 @@ def run_ours(args, wl):
                                                s_ptr))
         return fmas.value / (t * 1e-3)
 
-    dfma_rate = fma_rate(1, 2000)
-    ffma_rate = fma_rate(0, 100000)
+    dfma_rate = fma_rate(1, 1000)
+    ffma_rate = fma_rate(0, 50000)
     del slots
     pattern = pattern_ceilings(ceil, pts, n, view, npx, eps, stream, timed)
 
@@ -512,27 +517,34 @@ def run_ours(args, wl):
                                   "host": host_cpu(),
                                   "sample": f"first {sample_n} points of the workload, one full frame "
                                             f"(both passes and resolves), {t:.1f} s"}
+    # the batched and serving workloads, after the main timed region, on one GPU: their own timings, reported
+    # beside the frame (sub-results, not part of `value`)
+    if world == 1 and not args.no_batched:
+        result["batched"] = batched_results(args, 20_000_000, 64, [(640, 480), (1920, 1080), (3840, 2160)],
+                                            steps=max(4, min(args.steps, 20)), warmup=max(1, min(args.warmup, 3)))
+    if world == 1 and not args.no_serving:
+        result["serving"] = serving_results(args, args.requests, ("continuous_batching", "one_request_per_frame"),
+                                            100)
     print(json.dumps(result), flush=True)
     if dist:
         dist.destroy_process_group()
 
 
-def run_batched(args):
-    """Batched workload: 20M LIDAR points (seed 3), 64 seeded orbit poses at 640x480 / 1920x1080 / 3840x2160
-    (--views, --resolutions change both), basic and HQ frames. Plain path: per view one render call and one resolve call (clearing). Batched: one
-    pcr_batch frame (chunk culling, one persistent launch per pass, one resolve) replayed from a CUDA graph.
-    Both produce the same images (checked). value = point-views per second of the batched frame."""
+def batched_results(args, n, nv, res, steps, warmup):
+    """Batched workload: n LIDAR points (seed 3), nv seeded orbit poses cycling over the resolutions res, basic
+    and HQ frames. Three ways to render the same frame, all giving the same images (checked):
+      * single-view launches: per view one certified render call and one resolve (the library's own
+        one-view-per-launch path, the primary comparison);
+      * the plain FP64 path: the same with the depth in FP64 per point, as the paper computes it (secondary);
+      * the batched frame: one pcr_batch frame (chunk culling, one persistent launch per pass, one resolve),
+        autotuned (pcr_batch_autotune), replayed from a CUDA graph."""
     import torch
     import scenes
     from paper_1908_02681_gb300 import pcr
-    torch.cuda.set_device(0)
-    pcr.load()
-    n = args.points
     host = torch.empty((n, 4), dtype=torch.int32, pin_memory=True)
     scenes.lidar(n, 3, out=host)
     pts = host.cuda()
-    res = [tuple(int(x) for x in r.split("x")) for r in args.resolutions.split(",")]
-    nv = args.views
+    del host
     views = scenes.orbit_views(nv, 3, resolutions=res)
     stream = torch.cuda.Stream()
     results = {}
@@ -550,55 +562,71 @@ def run_batched(args):
                     pcr.pcr_render_atomicmin(fb, pts, v, stream)
                 pcr.pcr_resolve(fb, o, 0, True, stream)
 
-        # the plain path with the depth in FP64 as the paper computes it (PCR_TRANSFORM_FP64), one view
-        # per launch
         views_fp64 = [scenes.View(v.view_proj, v.near, v.far, v.width, v.height) for v in views]
         for v in views_fp64:
             v.transform = 1
         outs_fp64 = [torch.empty(v.width * v.height, dtype=torch.int32, device="cuda") for v in views]
 
-        def timed(fn, steps):
-            for _ in range(args.warmup):
+        def timed(fn, k):
+            for _ in range(warmup):
                 fn()
             stream.synchronize()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            for _ in range(steps):
+            for _ in range(k):
                 fn()
             b.record(stream)
             b.synchronize()
-            return a.elapsed_time(b) / steps
+            return a.elapsed_time(b) / k
 
         with torch.cuda.stream(stream):
-            t_plain = timed(plain_frame, max(2, args.steps // 4))
+            t_plain = timed(plain_frame, max(2, steps // 4))
             t_fp64 = timed(lambda: plain_frame(views_fp64, outs_fp64), 2)
             cloud = pcr.pcr_cloud_create(pts, stream)
             batch = pcr.pcr_batch_create(cloud, fbs, outs_batch, hq=hq, clear_after=True)
             pcr.pcr_batch_set_views(batch, views)
+            pcr.pcr_batch_set_tuning(batch, None)
             pcr.pcr_batch_capture(batch, stream)
-            t_batch = timed(lambda: pcr.pcr_batch_launch(batch, stream), args.steps)
+            t_default = timed(lambda: pcr.pcr_batch_launch(batch, stream), max(2, steps // 4))
+            tuning = pcr.pcr_batch_autotune(batch, stream, force=True)
+            pcr.pcr_batch_capture(batch, stream)
+            t_batch = timed(lambda: pcr.pcr_batch_launch(batch, stream), steps)
             stream.synchronize()
         same = all(bool((a == b).all()) for a, b in zip(outs_plain, outs_batch)) and \
             all(bool((a == b).all()) for a, b in zip(outs_fp64, outs_batch))
         visible = pcr.pcr_batch_visible_chunks(batch)
         mode = "hq" if hq else "basic"
-        results[mode] = {"plain_ms": t_plain, "batched_ms": t_batch, "speedup": t_plain / t_batch,
+        results[mode] = {"batched_ms": t_batch, "single_view_launches_ms": t_plain,
+                         "speedup_vs_single_view_launches": t_plain / t_batch,
                          "plain_fp64_ms": t_fp64, "speedup_vs_plain_fp64": t_fp64 / t_batch,
+                         "batched_default_tuning_ms": t_default, "autotuned": tuning,
                          "point_views_per_s": nv * n / (t_batch * 1e-3), "identical_images": same,
                          "visible_chunk_fraction": sum(visible) / (nv * ((n + 1023) // 1024))}
         batch.close()
         cloud.close()
         for fb in fbs:
             fb.close()
-    line = {"metric": f"batched frame: point-views/s ({nv} views, {n // 1_000_000}M points), speedup vs one view per "
-                      f"launch",
-            "value": results["basic"]["point_views_per_s"] / 1e9, "unit": "G point-views/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": results["basic"]["batched_ms"],
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64+f64",
-            "data": "synthetic",
-            "config": {"workload": f"LIDAR {n // 1_000_000}M points (seed 3), {nv} orbit poses (seed 3), "
-                                   f"{' / '.join(args.resolutions.split(','))} cycling, basic and HQ (eps 1%)"},
+    return {"config": {"workload": f"LIDAR {n // 1_000_000}M points (seed 3), {nv} orbit poses (seed 3), "
+                                   f"{' / '.join(f'{w}x{h}' for w, h in res)} cycling, basic and HQ (eps 1%)",
+                       "primary_comparison": "single-view certified launches (one view per launch)"},
             "modes": results}
+
+
+def run_batched(args):
+    """The batched workload alone (--workload batched): one JSON line, value = point-views/s of the basic frame."""
+    import torch
+    from paper_1908_02681_gb300 import pcr
+    torch.cuda.set_device(0)
+    pcr.load()
+    res = [tuple(int(x) for x in r.split("x")) for r in args.resolutions.split(",")]
+    r = batched_results(args, args.points, args.views, res, args.steps, args.warmup)
+    basic = r["modes"]["basic"]
+    line = {"metric": f"batched frame: point-views/s ({args.views} views, {args.points // 1_000_000}M points), "
+                      f"speedup vs one view per launch",
+            "value": basic["point_views_per_s"] / 1e9, "unit": "G point-views/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": basic["batched_ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64+f64",
+            "data": "synthetic", "config": r["config"], "modes": r["modes"]}
     print(json.dumps(line), flush=True)
 
 
@@ -637,7 +665,7 @@ def _serve_stream(pcr, server, cids, reqs, gaps_s, outs, keep):
     return [done[ids[i]] for i in range(len(reqs))]
 
 
-def run_serving(args):
+def serving_results(args, n_req, server_modes, k_plain):
     """Serving workload: 6 resident LIDAR clouds (10M, 25M, 50M, 100M, 200M, 500M points; seeds 10..15), a
     seeded Poisson request stream (mean gap 2 ms, seed 7), resolution uniform over 1280x720 / 1920x1080 /
     2560x1440 / 3840x2160, 70 % basic / 30 % HQ (eps 1 %), a seeded orbit pose per request. Served by
@@ -648,8 +676,6 @@ def run_serving(args):
     import torch
     import scenes
     from paper_1908_02681_gb300 import pcr
-    torch.cuda.set_device(0)
-    pcr.load()
     sizes = [10_000_000, 25_000_000, 50_000_000, 100_000_000, 200_000_000, 500_000_000]
     if args.serving_scale != 1.0:
         sizes = [max(1024, int(n * args.serving_scale)) for n in sizes]
@@ -662,7 +688,6 @@ def run_serving(args):
     del host
     res = [(1280, 720), (1920, 1080), (2560, 1440), (3840, 2160)]
     rng = np.random.default_rng(7)
-    n_req = args.requests
     gaps = rng.exponential(2e-3, n_req)
     cl = rng.integers(0, len(sizes), n_req)
     rs = rng.integers(0, len(res), n_req)
@@ -674,9 +699,9 @@ def run_serving(args):
     warm_reqs = [(k % len(sizes), views[k], k % 3 == 0, k % ring) for k in range(max(args.warmup, 1) * 4)]
     sample = set(range(0, n_req, max(1, n_req // 40)))
     results = {}
-    for name, streams, per_frame, cap in (("continuous_batching", 4, 64, 1_000_000_000),
-                                          ("continuous_batching_uncapped", 4, 64, 0),
-                                          ("one_request_per_frame", 1, 1, 0)):
+    all_modes = (("continuous_batching", 4, 64, 1_000_000_000), ("continuous_batching_uncapped", 4, 64, 0),
+                 ("one_request_per_frame", 1, 1, 0))
+    for name, streams, per_frame, cap in [m for m in all_modes if m[0] in server_modes]:
         server = pcr.pcr_server_create(streams, per_frame, 16 << 30, cap)
         cids = [pcr.pcr_server_add_cloud(server, c) for c in clouds]
         _serve_stream(pcr, server, cids, warm_reqs, [0.0] * len(warm_reqs), outs, None)
@@ -713,7 +738,7 @@ def run_serving(args):
             results[name]["sampled_identical_to_alone"] = f"{same}/{len(kept)}"
     # The plain path: each request rendered alone, one view per launch, the depth in FP64 as the paper
     # computes it (PCR_TRANSFORM_FP64), back to back on one stream, over a sample of the same requests.
-    k_plain = min(n_req, 300)
+    k_plain = min(n_req, k_plain)
     fb_plain = {}
 
     def plain_one(cloud, v, hq, out):
@@ -742,17 +767,33 @@ def run_serving(args):
     for fb in fb_plain.values():
         fb.close()
     cb, one = results["continuous_batching"], results["one_request_per_frame"]
-    line = {"metric": "served frames/s and latency (Poisson 2 ms mean gap, 6 resident clouds)",
-            "value": cb["frames_per_s"], "unit": "frames/s", "n_gpus": 1, "steps": n_req, "warmup": len(warm_reqs),
-            "ms_per_step": 1e3 / cb["frames_per_s"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+i64+f64", "data": "synthetic",
-            "config": {"workload": f"serving: clouds {[n // 1_000_000 for n in sizes]}M LIDAR points (seeds 10-15), "
+    del clouds, outs
+    torch.cuda.empty_cache()
+    return {"config": {"workload": f"serving: clouds {[n // 1_000_000 for n in sizes]}M LIDAR points (seeds 10-15), "
                                    f"{n_req} requests, Poisson mean gap 2 ms (seed 7), 720p-4K, 70% basic / 30% HQ"},
-            "p50_ms": cb["p50_ms"], "p99_ms": cb["p99_ms"], "modes": results,
+            "frames_per_s": cb["frames_per_s"], "p50_ms": cb["p50_ms"], "p99_ms": cb["p99_ms"],
+            "saturated_frames_per_s": cb["saturated_frames_per_s"], "modes": results,
             "saturated_speedup_vs_one_request_per_frame": cb["saturated_frames_per_s"] / one["saturated_frames_per_s"],
             "saturated_speedup_vs_plain_fp64": cb["saturated_frames_per_s"] /
-            results["plain_fp64_one_view_per_launch"]["saturated_frames_per_s"],
-            "clocks": cb["clocks"]}
+            results["plain_fp64_one_view_per_launch"]["saturated_frames_per_s"]}
+
+
+def run_serving(args):
+    """The serving workload alone (--workload serving): one JSON line, value = served frames/s (Poisson)."""
+    import torch
+    from paper_1908_02681_gb300 import pcr
+    torch.cuda.set_device(0)
+    pcr.load()
+    r = serving_results(args, args.requests, ("continuous_batching", "continuous_batching_uncapped",
+                                              "one_request_per_frame"), 300)
+    cb = r["modes"]["continuous_batching"]
+    line = {"metric": "served frames/s and latency (Poisson 2 ms mean gap, 6 resident clouds)",
+            "value": r["frames_per_s"], "unit": "frames/s", "n_gpus": 1, "steps": args.requests,
+            "warmup": max(args.warmup, 1) * 4, "ms_per_step": 1e3 / r["frames_per_s"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64+f64", "data": "synthetic",
+            "config": r["config"], "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"], "modes": r["modes"],
+            "saturated_speedup_vs_one_request_per_frame": r["saturated_speedup_vs_one_request_per_frame"],
+            "saturated_speedup_vs_plain_fp64": r["saturated_speedup_vs_plain_fp64"], "clocks": cb["clocks"]}
     print(json.dumps(line), flush=True)
 
 
@@ -766,6 +807,8 @@ def main():
     ap.add_argument("--transform", choices=["exact", "fp64", "double-float"], default="exact")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="default run: skip the batched sub-result")
+    ap.add_argument("--no-serving", action="store_true", help="default run: skip the serving sub-result")
     ap.add_argument("--cpu-sample", type=int, default=100_000_000)
     ap.add_argument("--reference-sample", type=int, default=0,
                     help="reference arm: at most this many points per frame (0: the workload's own count)")
