@@ -68,6 +68,11 @@ def _workload(name: str):
         return dict(desc="LIDAR 20M points (the 100M recipe at 20M points), 1920x1080, fov 60, near 0.1, far 3000, "
                          "40-bit linear depth, eps 1%",
                     n=20_000_000, gen=lambda n, out: scenes.lidar(n, 2, out=out), view=scenes.lidar_1km_view())
+    if name == "city400m":  # the precision study's scene
+        return dict(desc="city 400M points ([-5000, 5000]^2 m, 8000 boxes, street-level detail), 3840x2160, eye 1.7 m "
+                         "above the terrain, near 0.01, far 10000, 40-bit linear depth, eps 1%",
+                    n=400_000_000, gen=lambda n, out: scenes.lidar(n, 4, scenes.lidar_params_city(), out=out),
+                    view=scenes.city_view(4))
     if name == "cube1m":
         return dict(desc="1M points uniform in the unit cube, 640x480, fov 60, near 0.1, far 10, 40-bit linear depth",
                     n=1_000_000, gen=lambda n, out: scenes.cube(n, 1, out=out), view=scenes.cube_1m_view())
@@ -414,6 +419,15 @@ def run_ours(args, wl):
     per_kernel = {nm: sum(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps)) / args.steps
                   for i, nm in enumerate(names)}
     status = pcr.pcr_get_device_status(fb)
+    tier_counts = None
+    if args.transform == "exact":  # how the certified transform decided each point (one extra, untimed pass)
+        counts = torch.zeros(4, dtype=torch.int64, device=dev)
+        pcr.pcr_clear(fb, stream)
+        pcr.pcr_render_atomicmin_stats(fb, pts, view, counts, stream)
+        c = [int(x) for x in counts.cpu()]
+        tier_counts = {"tier1_exact": c[0], "tier1_undecided_code": c[1], "fp64_arbiter": c[2],
+                       "deferred_to_tier2": c[3]}
+        pcr.pcr_clear(fb, stream)
 
     # end to end through the C ABI with host buffers (pcr_render_frame_host): every step copies the 1.6 GB
     # of points from pinned host memory (in chunks, pass 1 starting on each chunk as it lands) and both
@@ -506,6 +520,7 @@ def run_ours(args, wl):
         "clocks": clocks.summary(),
         "gpu_launches": launches,
         "device_status": status,
+        "tier_counts": tier_counts,
     }
     if e2e:
         result["e2e"] = e2e
