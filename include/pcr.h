@@ -58,7 +58,10 @@ typedef struct {
  *   PIECEWISE: sub-ranges [lo_k, hi_k) at res_k codes per metre, codes of range k following those of
  *              range k-1: q = base_k + floor((w - lo_k) * res_k), base_k = sum_{j<k} ceil((hi_j - lo_j) * res_j);
  *              depths outside every range are culled (Section 2.1's nm / um / mm example).
- * In every mode q = min(q, 2^40 - 2), so that no key equals the empty value. */
+ * In every mode q = min(q, 2^40 - 2), so that no key equals the empty value. The EXACT transform evaluates all
+ * three in single precision with certified bounds (PIECEWISE with one depth table per range that meets
+ * [near, far); views whose piecewise codes can reach the cap, like the other views outside its
+ * preconditions, run on the FP64 kernels with the same results). */
 enum { PCR_DEPTH_LINEAR = 0, PCR_DEPTH_METRIC = 1, PCR_DEPTH_PIECEWISE = 2 };
 
 /* How the per-point transform is evaluated.
@@ -108,7 +111,7 @@ typedef struct {
 #define PCR_FB_HQ 1u /* also allocate the 16 B/pixel HQ accumulation buffer (needed by pcr_render_hq_splat) */
 
 /* Allocates a width x height framebuffer on the current device (keys: 8 B/pixel; with PCR_FB_HQ also
- * sums: 16 B/pixel; plus a 12 KB device copy of the depth table of the view last rendered, re-uploaded on
+ * sums: 16 B/pixel; plus a 96 KB device copy of the depth tables of the view last rendered, re-uploaded on
  * the render call's stream when the view changes) and clears it (synchronously). width, height in
  * 1..16384. */
 pcr_status pcr_create_framebuffer(int32_t width, int32_t height, uint32_t flags, pcr_framebuffer** out);
@@ -148,8 +151,9 @@ pcr_status pcr_render_atomicmin(pcr_framebuffer* fb, const pcr_point* d_points, 
  * EXACT transform's single-precision evaluation handled the points: [0] decided by the first tier (float
  * pixel estimate with its error bound, exact depth code), [1] depth code undecided between two
  * neighbours, [2] sent to the FP64 arbiter, [3] deferred to the second tier (double-float clip values).
- * All four stay 0 when the view is evaluated by the FP64 kernels (transform FP64, piecewise depth, or a
- * view outside the single-precision preconditions). A diagnostic of the transform; the framebuffer
+ * For PIECEWISE depth the points the first tier leaves undecided go to the FP64 arbiter directly ([2] and [3]
+ * then count the same points). All four stay 0 when the view is evaluated by the FP64 kernels (transform
+ * FP64, or a view outside the single-precision preconditions). A diagnostic of the transform; the framebuffer
  * result is the same as pcr_render_atomicmin's. */
 pcr_status pcr_render_atomicmin_stats(pcr_framebuffer* fb, const pcr_point* d_points, uint64_t n,
                                       const pcr_view* view, uint64_t* d_counts, pcr_stream_t stream);

@@ -155,16 +155,19 @@ pcr_status after_launch(const char* what, uint64_t launches = 1) {
   return e == cudaSuccess ? PCR_OK : cuda_fail(e, what);
 }
 
-// The device copy of the view's depth table for the certified passes on fb (uploaded on `s` when the view
-// differs from the last one), or null (double-float transform, FP64 kernels, or the upload failed: the
-// passes then read the table from their parameter block).
+// The device copy of the view's depth tables for the certified passes on fb (uploaded on `s` when the view
+// differs from the last one; one table, or one per PIECEWISE range), or null (double-float transform, FP64
+// kernels, or the upload failed: LINEAR and METRIC passes then read the table from their parameter block,
+// PIECEWISE views run on the FP64 kernels).
 const long long* fb_table(pcr_framebuffer* fb, const pcr::DevView& dv, int transform, cudaStream_t s) {
   if (transform != PCR_TRANSFORM_EXACT) return nullptr;
   const pcr::CertParams* P = nullptr;
-  if (!pcr::cached_cert(dv, false, &P)) return nullptr;
+  const long long* tables = nullptr;
+  if (!pcr::cached_cert(dv, false, &P, &tables)) return nullptr;
   if (!fb->table_valid || std::memcmp(&fb->table_view, &dv, sizeof(dv)) != 0) {
     fb->table_valid = false;
-    if (cudaMemcpyAsync(fb->d_table, &P->F[0][0], sizeof(P->F), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+    if (cudaMemcpyAsync(fb->d_table, tables, pcr::table_blocks(*P) * sizeof(P->F), cudaMemcpyHostToDevice, s) !=
+        cudaSuccess) {
       cudaGetLastError();
       return nullptr;
     }
@@ -228,7 +231,7 @@ pcr_status pcr_create_framebuffer(int32_t width, int32_t height, uint32_t flags,
   e = cudaMalloc(&fb->keys, npx * sizeof(unsigned long long));
   if (e == cudaSuccess && (flags & PCR_FB_HQ)) e = cudaMalloc(&fb->accum, npx * sizeof(ulonglong2));
   if (e == cudaSuccess) e = cudaMalloc(&fb->status, 256);
-  if (e == cudaSuccess) e = cudaMalloc(&fb->d_table, sizeof(pcr::CertParams::F));
+  if (e == cudaSuccess) e = cudaMalloc(&fb->d_table, pcr::kMaxRanges * sizeof(pcr::CertParams::F));
   if (e != cudaSuccess) {
     cudaGetLastError();
     cudaFree(fb->keys);
@@ -396,10 +399,25 @@ pcr_status pcr_project_points(const pcr_point* d_points, uint64_t n, const pcr_v
   unsigned long long* keys = reinterpret_cast<unsigned long long*>(d_key);
   const unsigned grid = grid_for(n, 256, device, 8);
   const pcr::CertParams* P = nullptr;
+  const long long* tables = nullptr;
   const bool approx = view->transform == PCR_TRANSFORM_DOUBLE_FLOAT;
-  if (view->transform == PCR_TRANSFORM_FP64 || !pcr::cached_cert(dv, approx, &P))
+  if (view->transform == PCR_TRANSFORM_FP64 || !pcr::cached_cert(dv, approx, &P, &tables)) {
     pcr::k_project_fp64<<<grid, 256, 0, s>>>(pts, n, dv, d_pixel, keys);
-  else if (approx)
+  } else if (P->n_pw > 0) {
+    // PIECEWISE: the ranges' tables in a stream-ordered temporary device copy
+    const size_t bytes = (size_t)P->n_pw * sizeof(P->F);
+    void* d_tab = nullptr;
+    cudaError_t e = cudaMallocAsync(&d_tab, bytes, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_tab, tables, bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+      auto kernel = P->n_pw > 2 ? pcr::k_project_cert<false, 2> : pcr::k_project_cert<false, 1>;
+      e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      if (e == cudaSuccess) kernel<<<grid, 256, bytes, s>>>(pts, n, *P, d_pixel, keys, (const long long*)d_tab);
+      if (e == cudaSuccess) e = cudaGetLastError();
+    }
+    if (d_tab) cudaFreeAsync(d_tab, s);
+    if (e != cudaSuccess) return cuda_fail(e, "piecewise projection");
+  } else if (approx)
     pcr::k_project_cert<true><<<grid, 256, 0, s>>>(pts, n, *P, d_pixel, keys);
   else
     pcr::k_project_cert<false><<<grid, 256, 0, s>>>(pts, n, *P, d_pixel, keys);

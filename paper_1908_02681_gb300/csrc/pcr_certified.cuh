@@ -72,6 +72,14 @@ struct CertParams {
   float near_h, near_l, far_h, far_l, S_h, S_l;
   int32_t approximate;
   int32_t linear;
+  // PIECEWISE depth: the n_pw ranges that meet [near, far) (0: LINEAR or METRIC). Range r has its own depth
+  // table (block r of the device table, 3 * kTableEntries entries each), window, code margin and first code.
+  int32_t n_pw;
+  float pw_wc[kMaxRanges], pw_whk[kMaxRanges], pw_kd[kMaxRanges], pw_hd0[kMaxRanges];
+  float pw_start[kMaxRanges];         // ascending split points: range r is the only one whose window may hold
+                                      // a w at or above pw_start[r] and below pw_start[r + 1]
+  unsigned long long pw_BL[kMaxRanges];  // (B_r + base_r 2^40) = BH 2^32 + BL: the first code folded in
+  long long pw_BH[kMaxRanges];
   DevView v;                          // the FP64 definition (for the arbiter)
   long long F[3][kTableEntries];      // t-row fixed-point coefficients, index (sign << 8) | exponent
 };
@@ -265,50 +273,134 @@ inline bool tier1_constants(const DevView& v, double S, CertParams* P) {
   return true;
 }
 
-// Fills P for the view; false when the view is outside the certified evaluation's preconditions (the
-// caller then uses the FP64 kernels, which accept every valid view).
-inline bool prepare_cert(const DevView& v, bool approximate, CertParams* P) {
-  std::memset(P, 0, sizeof(*P));
-  P->v = v;
-  P->approximate = approximate ? 1 : 0;
-  if (v.depth_mode != 0 && v.depth_mode != 1) return false;  // piecewise: FP64 kernels
-  P->linear = v.depth_mode == 0;
-  if (!(v.near_ >= 0x1p-60) || !(v.far_ < 0x1p100)) return false;
-  for (int r = 0; r < 3; ++r)
-    for (int c = 0; c < 4; ++c)
-      if (!split_float(v.m[4 * r + c], &P->H[r][c], &P->L[r][c])) return false;
-  P->kappa = 40.0f * 0x1p-48f * (1.0f + 0x1p-20f);
-  const double S = v.scale;
-  if (!(S > 0.0) || !(S < 0x1p100)) return false;
-  two_float(v.near_, &P->near_h, &P->near_l);
-  two_float(v.far_, &P->far_h, &P->far_l);
-  two_float(S, &P->S_h, &P->S_l);
-  // t = sum_j A_j X_j + B, A_j = S * M[3][j], B = S * (M[3][3] - near) (LINEAR) or S * M[3][3] (METRIC)
-  const double* m3 = v.m + 8;
+// The fixed-point depth table of t = S (w - off): F[j][(sign << 8) | e] = round(S M[3][j] 2^(e - 150) 2^40) for
+// every sign and biased exponent of coordinate j (0 past the largest usable exponent, which goes to e_max[j]),
+// and b = S (M[3][3] - off) 2^40 rounded. False when the scale puts the values out of the representable range.
+inline bool build_table(double S, const double* m3, double off, long long (*F)[kTableEntries], int32_t* e_max,
+                        __int128* b_out) {
   for (int j = 0; j < 3; ++j) {
     const double a = S * m3[j];
     if (!(std::fabs(a) < 0x1p80)) return false;  // keeps the subnormal shortcut's error below 2^-46
-    P->Af[j] = (float)a;
-    P->e_max[j] = 254;
+    e_max[j] = 254;
     for (int e = 0; e < kTableExp; ++e) {
       const int ee = e == 0 ? 1 : e;  // subnormals share exponent 1's scale (see the device loop)
       __int128 f;
       const bool ok = e < 255 && fixed_mul(S, m3[j], ee - 150 + kFixedFracBits, &f) &&
                       f < ((__int128)1 << 62) && f > -((__int128)1 << 62);
       if (!ok) {
-        if (P->e_max[j] >= e) P->e_max[j] = e - 1;
+        if (e_max[j] >= e) e_max[j] = e - 1;
         f = 0;
       }
-      P->F[j][e] = (long long)f;
-      P->F[j][kTableExp + e] = -(long long)f;
+      F[j][e] = (long long)f;
+      F[j][kTableExp + e] = -(long long)f;
     }
-    if (P->e_max[j] < 127) return false;  // coordinates of magnitude 1 would not be usable
+    if (e_max[j] < 127) return false;  // coordinates of magnitude 1 would not be usable
   }
   __int128 b, bn = 0;
   if (!fixed_mul(S, m3[3], kFixedFracBits, &b)) return false;
-  if (P->linear && !fixed_mul(S, v.near_, kFixedFracBits, &bn)) return false;
+  if (off != 0.0 && !fixed_mul(S, off, kFixedFracBits, &bn)) return false;
   b -= bn;
   if (b >= ((__int128)1 << 94) || b <= -((__int128)1 << 94)) return false;
+  *b_out = b;
+  return true;
+}
+
+// |x| + |y| + |z| below this keeps every coordinate at or below the smallest e_max (table entries usable).
+inline float xyz_limit(const int32_t* e_max) {
+  int emin = 254;
+  for (int j = 0; j < 3; ++j) emin = e_max[j] < emin ? e_max[j] : emin;
+  if (emin >= 254) return 3.0e38f;
+  return std::ldexp(1.0f, emin - 127 + 1 > 127 ? 127 : emin - 127 + 1);  // 2^(e+1): exponent <= e
+}
+
+// Tier-1 constants of one PIECEWISE range r (t = res (w - lo), codes base + floor(t)), for the part
+// [lo_e, hi_e) of the range inside [near, far): the depth window (as in tier1_constants, with the range's
+// scale and offset), the code margin, the first code. False when the range's codes could reach the cap.
+inline bool piecewise_range(double res, double lo, double lo_e, double hi_e, double base, const double* m3,
+                            double m3max, CertParams* P, int r) {
+  const double u = 0x1p-24, v53 = 0x1p-53;
+  const double t_lo = 2.5, t_hi = 1099511627776.0 - 33554432.0;
+  const double w_lo = lo + t_lo / res, w_hi = lo + t_hi / res;
+  const double nin = std::fmax(lo_e * (1.0 + 4.0 * u), w_lo * (1.0 + 4.0 * u));
+  const double fin = std::fmin(hi_e * (1.0 - 4.0 * u), w_hi * (1.0 - 4.0 * u));
+  if (fin > nin) {
+    P->pw_wc[r] = (float)(0.5 * (nin + fin));
+    const double wh = std::fmin((double)P->pw_wc[r] - nin, fin - (double)P->pw_wc[r]);
+    const double whk = (wh - (double)P->kw3) / (1.0 + 2.0001 * u);
+    P->pw_whk[r] = whk > 0.0 ? f_down(whk) : 0.0f;
+  } else {
+    P->pw_wc[r] = 0.0f;
+    P->pw_whk[r] = 0.0f;
+  }
+  P->pw_start[r] = f_down(nin);
+  // every code of the range stays below the cap: base + (hi_e - lo) res + 2 < 2^40 - 2
+  if (!(base + (hi_e - lo) * res * (1.0 + 0x1p-40) + 4.0 < (double)kQMax)) return false;
+  P->pw_kd[r] = f_up(5.2 * v53 * res * m3max * (1.0 + 2.0001 * u) * (1.0 + 0x1p-18));
+  const double d0 = 5.2 * v53 * res * (std::fabs(m3[3]) + lo) * (1.0 + 0x1p-18) + 3.1 * v53 * res * lo + 0x1p-13;
+  P->pw_hd0[r] = f_down(0.5 - d0 - 0x1p-22);
+  return true;
+}
+
+// Fills P for the view; false when the view is outside the certified evaluation's preconditions (the
+// caller then uses the FP64 kernels, which accept every valid view). tables (may be null): receives the
+// depth tables, block r for PIECEWISE range r (block 0 is P->F for LINEAR and METRIC).
+inline bool prepare_cert(const DevView& v, bool approximate, CertParams* P,
+                         long long (*tables)[3][kTableEntries] = nullptr) {
+  std::memset(P, 0, sizeof(*P));
+  P->v = v;
+  P->approximate = approximate ? 1 : 0;
+  const bool pw = v.depth_mode == 2;
+  if (v.depth_mode != 0 && v.depth_mode != 1 && !pw) return false;
+  if (pw && (approximate || !tables)) return false;  // piecewise: the exact transform with device tables only
+  P->linear = v.depth_mode != 1;
+  if (!(v.near_ >= 0x1p-60) || !(v.far_ < 0x1p100)) return false;
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 4; ++c)
+      if (!split_float(v.m[4 * r + c], &P->H[r][c], &P->L[r][c])) return false;
+  P->kappa = 40.0f * 0x1p-48f * (1.0f + 0x1p-20f);
+  const double* m3 = v.m + 8;
+  if (pw) {
+    // the ranges meeting [near, far), each a LINEAR-like sub-problem with scale res and offset lo
+    double m3max = 0.0;
+    for (int j = 0; j < 3; ++j) m3max = std::fmax(m3max, std::fabs(m3[j]));
+    int n = 0;
+    int32_t emin[3] = {254, 254, 254};
+    for (int k = 0; k < v.n_ranges; ++k) {
+      const double lo_e = std::fmax(v.lo[k], v.near_), hi_e = std::fmin(v.hi[k], v.far_);
+      if (!(hi_e > lo_e)) continue;
+      const double res = v.res[k];
+      if (!(res > 0.0) || !(res < 0x1p100)) return false;
+      if (n == 0) {  // the shared tier-1 constants (the scale only enters the window and margin, set per range)
+        if (!tier1_constants(v, res, P)) return false;
+      }
+      int32_t em[3];
+      __int128 b;
+      if (!build_table(res, m3, v.lo[k], tables[n], em, &b)) return false;
+      for (int j = 0; j < 3; ++j) emin[j] = em[j] < emin[j] ? em[j] : emin[j];
+      b += (__int128)(unsigned long long)v.base[k] << kFixedFracBits;  // codes of range k start at base_k
+      P->pw_BL[n] = (unsigned long long)(uint32_t)(unsigned __int128)b;
+      P->pw_BH[n] = (long long)(b >> 32);
+      if (!piecewise_range(res, v.lo[k], lo_e, hi_e, v.base[k], m3, m3max, P, n)) return false;
+      ++n;
+    }
+    if (n == 0) return false;  // nothing of [near, far) has a code: every point is culled (FP64 kernels)
+    if (n == 1) P->pw_start[1] = 3.4e38f * 2.0f;  // +inf: the second of two selectable ranges never applies
+    P->n_pw = n;
+    P->xyz_max = xyz_limit(emin);
+    std::memcpy(P->F, tables[0], sizeof(P->F));
+    P->BL = P->pw_BL[0];
+    P->BH = P->pw_BH[0];
+    return true;
+  }
+  const double S = v.scale;
+  if (!(S > 0.0) || !(S < 0x1p100)) return false;
+  two_float(v.near_, &P->near_h, &P->near_l);
+  two_float(v.far_, &P->far_h, &P->far_l);
+  two_float(S, &P->S_h, &P->S_l);
+  // t = sum_j A_j X_j + B, A_j = S * M[3][j], B = S * (M[3][3] - near) (LINEAR) or S * M[3][3] (METRIC)
+  for (int j = 0; j < 3; ++j) P->Af[j] = (float)(S * m3[j]);
+  __int128 b;
+  if (!build_table(S, m3, P->linear ? v.near_ : 0.0, P->F, P->e_max, &b)) return false;
   const unsigned __int128 bu = (unsigned __int128)b;
   P->B0 = (uint32_t)bu;
   P->B1 = (uint32_t)(bu >> 32);
@@ -324,12 +416,7 @@ inline bool prepare_cert(const DevView& v, bool approximate, CertParams* P) {
   P->t_c1 = (float)(5.2 * u64 * (1.0 + 0x1p-18));
   P->t_c2 = (float)((P->linear ? 3.1 * u64 * S * v.near_ : 0.0) + 0x1p-13);
   if (!tier1_constants(v, S, P)) return false;
-  {
-    int emin = 254;
-    for (int j = 0; j < 3; ++j) emin = P->e_max[j] < emin ? P->e_max[j] : emin;
-    P->xyz_max = std::ldexp(1.0f, emin - 127 + 1 > 127 ? 127 : emin - 127 + 1);  // 2^(e+1): exponent <= e
-    if (emin >= 254) P->xyz_max = 3.0e38f;
-  }
+  P->xyz_max = xyz_limit(P->e_max);
   // depth-cull thresholds: T_n, T_f are the FP64 codes of the near and far planes (monotone rounding:
   // t > T_n => w >= near, t < T_n => w < near, t < T_f => w < far, t > T_f => w >= far)
   const double Tn = P->linear ? 0.0 : v.near_ * S;
@@ -339,6 +426,7 @@ inline bool prepare_cert(const DevView& v, bool approximate, CertParams* P) {
   P->qn_cull = (long long)std::floor(Tn) - 1;
   P->qf_safe = (long long)std::floor(Tf) - 1;
   P->qf_cull = (long long)std::floor(Tf) + 1;
+  if (tables) std::memcpy(tables[0], P->F, sizeof(P->F));
   return true;
 }
 
@@ -442,6 +530,10 @@ __device__ __forceinline__ uint32_t depth_decision(const CertParams& P, long lon
 // shared-memory copy of P.F.
 __device__ __forceinline__ CertFrag classify_cert(const CertParams& P, const long long* __restrict__ F, uint4 p) {
   CertFrag out{kCulled, 0u, 0};
+  if (P.n_pw) {  // PIECEWISE: a point tier 1 could not decide goes to the FP64 definition
+    out.state = kHard;
+    return out;
+  }
   const uint32_t bx = p.x, by = p.y, bz = p.z;
   const uint32_t ex = (bx >> 23) & 0xFFu, ey = (by >> 23) & 0xFFu, ez = (bz >> 23) & 0xFFu;
   // any NaN or infinite coordinate makes w NaN or infinite in FP64: culled
@@ -515,7 +607,11 @@ __device__ __forceinline__ unsigned long long code_from_fixed(uint32_t a1, uint3
 // point it does not certify takes the branch that tests whether it is certainly culled.
 // PP: CertParams (single-view kernels, read from the kernel parameter block) or HotParams (batched
 // kernels, which hold one view's first-tier constants in registers); both have the fields used here.
-template <typename PP>
+// kPw (PIECEWISE depth, CertParams only): the range whose window certainly holds w gives the table (block r of
+// F), the fixed-point offset (with the range's first code folded in: base 2^40 only changes bits 40 and up,
+// not the fraction) and the margin. Outside every window: undecided.
+// kPw = 1: at most two ranges, whose constants are picked by selects (no indexed constant loads); 2: any number.
+template <typename PP, int kPw = 0>
 __device__ __forceinline__ FastFrag classify_fast(const PP& P, const long long* __restrict__ F, uint4 p) {
   const float x = __uint_as_float(p.x), y = __uint_as_float(p.y), z = __uint_as_float(p.z);
   // finite, and inside the exponent range whose table entries exist (else tier 2 decides): the rounded sum of
@@ -524,16 +620,48 @@ __device__ __forceinline__ FastFrag classify_fast(const PP& P, const long long* 
   const bool in_range = s < P.xyz_max;
   // w estimate (fma chain, as the FP64 definition orders it) and the depth window: |w - wc| + Delta < wh
   const float w = __fmaf_rn(P.Wr[2], z, __fmaf_rn(P.Wr[1], y, __fmaf_rn(P.Wr[0], x, P.Wr[3])));
-  const bool depth_in = fabsf(__fsub_rn(w, P.wc)) < __fmaf_rn(-P.kw, s, P.whk);
+  bool depth_in;
+  unsigned long long BL;
+  long long BH;
+  float kd, hd0;
+  int kk = 0;  // PIECEWISE: the range
+  (void)kk;
+  if constexpr (kPw == 1) {
+    // one or two ranges (a single range has pw_start[1] = +inf): selects between the two sets of constants
+    const bool second = w >= P.pw_start[1];
+    kk = second ? 1 : 0;
+    depth_in = fabsf(__fsub_rn(w, second ? P.pw_wc[1] : P.pw_wc[0])) <
+               __fmaf_rn(-P.kw, s, second ? P.pw_whk[1] : P.pw_whk[0]);
+    F += second ? 3 * kTableEntries : 0;
+    BL = second ? P.pw_BL[1] : P.pw_BL[0];
+    BH = second ? P.pw_BH[1] : P.pw_BH[0];
+    kd = second ? P.pw_kd[1] : P.pw_kd[0];
+    hd0 = second ? P.pw_hd0[1] : P.pw_hd0[0];
+  } else if constexpr (kPw == 2) {
+    // the windows are disjoint and ascending: only the last one starting at or below w can hold it
+    for (int r = 1; r < P.n_pw; ++r) kk += w >= P.pw_start[r];
+    depth_in = fabsf(__fsub_rn(w, P.pw_wc[kk])) < __fmaf_rn(-P.kw, s, P.pw_whk[kk]);
+    F += kk * (3 * kTableEntries);
+    BL = P.pw_BL[kk];
+    BH = P.pw_BH[kk];
+    kd = P.pw_kd[kk];
+    hd0 = P.pw_hd0[kk];
+  } else {
+    depth_in = fabsf(__fsub_rn(w, P.wc)) < __fmaf_rn(-P.kw, s, P.whk);
+    BL = P.BL;
+    BH = P.BH;
+    kd = P.kd;
+    hd0 = P.hd0;
+  }
   // ---- depth code: t * 2^40 = sum m_j F_j + B, accumulated as sum m_j F_lo_j + 2^32 sum m_j F_hi_j
   const long long fx_ = F[p.x >> 23], fy_ = F[kTableEntries + (p.y >> 23)], fz_ = F[2 * kTableEntries + (p.z >> 23)];
   const uint32_t mx = (p.x & 0x7FFFFFu) | 0x800000u, my = (p.y & 0x7FFFFFu) | 0x800000u,
                  mz = (p.z & 0x7FFFFFu) | 0x800000u;
-  unsigned long long L = P.BL;
+  unsigned long long L = BL;
   L += (unsigned long long)mx * (uint32_t)fx_;
   L += (unsigned long long)my * (uint32_t)fy_;
   L += (unsigned long long)mz * (uint32_t)fz_;
-  long long Hh = P.BH;
+  long long Hh = BH;
   Hh += (long long)(int32_t)mx * (long long)(int32_t)(fx_ >> 32);
   Hh += (long long)(int32_t)my * (long long)(int32_t)(fy_ >> 32);
   Hh += (long long)(int32_t)mz * (long long)(int32_t)(fz_ >> 32);
@@ -549,10 +677,11 @@ __device__ __forceinline__ FastFrag classify_fast(const PP& P, const long long* 
   // hD = RN(hd0 - kd s), hd0 = RD(1/2 - d0 - 2^-22), is within 2^-25 of its real value, so |frac - 1/2| < hD
   // (frac - 1/2 is exact) gives D + 2^-22 - 2^-25 < frac and frac + 2^-23 < 1 - D. hD > 1/4 gives D < 1/4:
   // an undecided code still has two usable candidates.
-  const float hD = __fmaf_rn(-P.kd, s, P.hd0);
+  const float hD = __fmaf_rn(-kd, s, hd0);
   const bool exact = fabsf(__fsub_rn(frac, 0.5f)) < hD;
   out.lo_half = frac < 0.5f;
   const bool amb_ok = hD > 0.25f;
+
   // ---- pixel estimate: gx = w (fx - 1/2), gy = w (fy - 1/2) up to the rounding bounds; with wf > 0 (depth_in)
   // fm = g * rcp(wf) and the bound hE = RN(he0 - (ke s + ke3) rcp(wf)) <= 1/2 - E - 2^-25
   const float gx = __fmaf_rn(P.Gx[2], z, __fmaf_rn(P.Gx[1], y, __fmaf_rn(P.Gx[0], x, P.Gx[3])));
@@ -900,20 +1029,28 @@ __device__ __forceinline__ void defer_points(bool defer, const uint4& p, uint4* 
 
 // Pass 1 (Section 2.1) with the certified transform. Tier 1 handles nearly every point; the others are
 // queued per warp in shared memory and handled 32 at a time by tier 2 and the FP64 arbiter. The points
-// arrive through the warp's bulk-copy ring (stream_tiles).
-template <bool kApprox, bool kMerge, bool kStats, bool kRing>
+// arrive through stream_tiles (direct loads or bulk-copy rings). kPw > 0: PIECEWISE depth (see classify_fast),
+// the ranges' tables in dynamic shared memory (P.n_pw blocks of 3 * kTableEntries entries, from the device table).
+template <bool kApprox, bool kMerge, bool kStats, bool kRing, int kPw>
 __global__ void __launch_bounds__(kCertThreads, kApprox ? PCR_CERT_APPROX_MIN_BLOCKS : PCR_CERT_MIN_BLOCKS) k_raster_cert(
     const uint4* __restrict__ pts, uint64_t n, const __grid_constant__ CertParams P,
     unsigned long long* __restrict__ keys, unsigned long long* __restrict__ stats, uint32_t* __restrict__ status,
     const long long* __restrict__ table) {
-  __shared__ long long sF[3 * kTableEntries];
+  __shared__ long long sF_static[kPw ? 1 : 3 * kTableEntries];
+  extern __shared__ __align__(16) long long sF_dynamic[];
   __shared__ uint4 queue[kCertWarps][kQueue];
   __shared__ __align__(128) uint4 ring[kCertWarps][2][kTile];
   __shared__ __align__(8) uint64_t bars[kCertWarps][2];
+  long long* const sF = kPw ? sF_dynamic : sF_static;
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   if (kRing && lane == 0) ring_init(bars[warp]);
   __syncwarp();
-  if (!kApprox) load_table(P, table, sF);
+  if constexpr (kPw) {
+    for (int i = threadIdx.x; i < P.n_pw * 3 * kTableEntries; i += blockDim.x) sF[i] = table[i];
+    __syncthreads();
+  } else if (!kApprox) {
+    load_table(P, table, sF);
+  }
   uint4* q = queue[warp];
   uint32_t qn = 0;
   unsigned c_exact = 0, c_amb = 0, c_fp64 = 0, c_defer = 0;
@@ -931,7 +1068,7 @@ __global__ void __launch_bounds__(kCertThreads, kApprox ? PCR_CERT_APPROX_MIN_BL
         pix = f.pixel;
         key = make_key((unsigned long long)f.q, p.w);
       } else {
-        const FastFrag f = classify_fast(P, sF, p);
+        const FastFrag f = classify_fast<CertParams, kPw>(P, sF, p);
         pix = f.pixel;
         key = key_from_fixed(f.a0, f.a1, f.a2, p.w);
         has = f.state == kExact;
@@ -1122,14 +1259,42 @@ inline unsigned persistent_grid(int resident, uint64_t n, int sms, int per_sm) {
   return cert_grid(n, sms, per_sm < resident ? per_sm : resident);
 }
 
-// table: device copy of P.F (or null: the kernels read it from the parameter block).
+// table: device copy of P.F (or null: the kernels read it from the parameter block); for PIECEWISE views
+// (P.n_pw > 0) the device copy of all the ranges' tables, required.
+template <bool kApprox, bool kMerge, bool kStats, bool kRing, int kPw>
+inline void raster_launch5(const uint4* pts, uint64_t n, const CertParams& P, unsigned long long* keys,
+                           unsigned long long* stats, uint32_t* status, int sms, int per_sm, cudaStream_t s,
+                           const long long* table) {
+  auto kernel = k_raster_cert<kApprox, kMerge, kStats, kRing, kPw>;
+  if constexpr (kPw) {
+    // the ranges' tables in dynamic shared memory: up to kMaxRanges * 12 KB (opt in above 48 KB once)
+    static const bool opted = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)(kMaxRanges * sizeof(P.F))) == cudaSuccess;
+    (void)opted;
+    const size_t dyn = (size_t)P.n_pw * sizeof(P.F);
+    int resident = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, kernel, kCertThreads, dyn) != cudaSuccess ||
+        resident < 1) {
+      cudaGetLastError();
+      resident = 1;
+    }
+    kernel<<<persistent_grid(resident, n, sms, per_sm), kCertThreads, dyn, s>>>(pts, n, P, keys, stats, status, table);
+  } else {
+    static const int resident = resident_blocks(kernel);  // per instantiation
+    kernel<<<persistent_grid(resident, n, sms, per_sm), kCertThreads, 0, s>>>(pts, n, P, keys, stats, status, table);
+  }
+}
+
 template <bool kApprox, bool kMerge, bool kStats, bool kRing>
 inline void raster_launch4(const uint4* pts, uint64_t n, const CertParams& P, unsigned long long* keys,
                            unsigned long long* stats, uint32_t* status, int sms, int per_sm, cudaStream_t s,
                            const long long* table) {
-  static const int resident = resident_blocks(k_raster_cert<kApprox, kMerge, kStats, kRing>);  // per instantiation
-  const unsigned grid = persistent_grid(resident, n, sms, per_sm);
-  k_raster_cert<kApprox, kMerge, kStats, kRing><<<grid, kCertThreads, 0, s>>>(pts, n, P, keys, stats, status, table);
+  if (!kApprox && P.n_pw > 2)
+    raster_launch5<false, kMerge, kStats, kRing, 2>(pts, n, P, keys, stats, status, sms, per_sm, s, table);
+  else if (!kApprox && P.n_pw > 0)
+    raster_launch5<false, kMerge, kStats, kRing, 1>(pts, n, P, keys, stats, status, sms, per_sm, s, table);
+  else
+    raster_launch5<kApprox, kMerge, kStats, kRing, 0>(pts, n, P, keys, stats, status, sms, per_sm, s, table);
 }
 
 // Pass 1 with the tuning's staging; the tier counters (stats) only with the exact transform, no merging.
@@ -1148,19 +1313,27 @@ inline void raster_launch(const uint4* pts, uint64_t n, const CertParams& P, uns
 // The certified constants of a view, prepared on this thread and kept for the next call with the same view
 // and mode (prepare_cert builds a 12 KB exact table: ~14 us of host time per call). Returns false when the
 // view is outside the single-precision preconditions.
-inline bool cached_cert(const DevView& v, bool approximate, const CertParams** out) {
+// tables (optional): the view's depth tables, block r for PIECEWISE range r (P->n_pw blocks; one for LINEAR
+// and METRIC), to be copied to the device.
+inline bool cached_cert(const DevView& v, bool approximate, const CertParams** out,
+                        const long long** tables = nullptr) {
   static thread_local CertParams P;
+  static thread_local long long T[kMaxRanges][3][kTableEntries];
   static thread_local DevView last_v;
   static thread_local int last = -1;  // -1: nothing cached; else approximate (0/1) of the cached view
   static thread_local bool last_ok = false;
   if (last != (approximate ? 1 : 0) || std::memcmp(&last_v, &v, sizeof(DevView)) != 0) {
-    last_ok = host::prepare_cert(v, approximate, &P);
+    last_ok = host::prepare_cert(v, approximate, &P, T);
     std::memcpy(&last_v, &v, sizeof(DevView));
     last = approximate ? 1 : 0;
   }
   *out = &P;
+  if (tables) *tables = &T[0][0][0];
   return last_ok;
 }
+
+// Blocks of the depth tables of prepared constants (the device copy's size in tables of 3 * kTableEntries).
+inline int table_blocks(const CertParams& P) { return P.n_pw > 0 ? P.n_pw : 1; }
 
 // Pass 1 for a view with n >= 1 points. status: the framebuffer's status word (timeout bit).
 inline bool launch_raster_certified(const uint4* pts, uint64_t n, const DevView& v, bool approximate,
@@ -1169,7 +1342,8 @@ inline bool launch_raster_certified(const uint4* pts, uint64_t n, const DevView&
                                     const long long* table = nullptr) {
   const CertParams* Pp = nullptr;
   const unsigned grid = cert_grid(n, sms, t.blocks_per_sm);
-  if (!cached_cert(v, approximate, &Pp)) {
+  // PIECEWISE views need the device copy of their tables
+  if (!cached_cert(v, approximate, &Pp) || (Pp->n_pw > 0 && table == nullptr)) {
     k_raster_fp64<<<grid, 256, 0, s>>>(pts, n, v, keys);
     return true;
   }
@@ -1208,7 +1382,7 @@ inline bool launch_hq_certified(const uint4* pts, uint64_t n, const DevView& v, 
                                 const Tuning& t = Tuning(), const long long* table = nullptr) {
   const CertParams* Pp = nullptr;
   const unsigned grid = cert_grid(n, sms, t.blocks_per_sm);
-  if (!cached_cert(v, approximate, &Pp)) {
+  if (!cached_cert(v, approximate, &Pp) || Pp->n_pw > 0) {  // (HQ takes LINEAR or METRIC views only)
     k_hq_fp64<<<grid, 256, 0, s>>>(pts, n, v, keys, accum, eps_num, eps_den);
     return true;
   }

@@ -11,14 +11,23 @@ namespace pcr {
 
 // EXACT (kApprox = false): tier 1 decides nearly every point; a point it cannot decide goes through tier 2
 // and, if that cannot decide either, through the FP64 definition. DOUBLE_FLOAT (kApprox = true): the
-// double-float evaluation alone. The depth table is read from the kernel parameter block.
-template <bool kApprox>
+// double-float evaluation alone. The depth table is read from the kernel parameter block; kPw (PIECEWISE
+// depth): the ranges' tables from the device copy `table` into dynamic shared memory.
+template <bool kApprox, int kPw = 0>
 __global__ void __launch_bounds__(256) k_project_cert(const uint4* __restrict__ pts, uint64_t n,
                                                       const __grid_constant__ CertParams P,
                                                       uint32_t* __restrict__ pix_out,
-                                                      unsigned long long* __restrict__ key_out) {
-  __shared__ long long sF[3 * kTableEntries];
-  if (!kApprox) load_table(P, sF);
+                                                      unsigned long long* __restrict__ key_out,
+                                                      const long long* __restrict__ table = nullptr) {
+  __shared__ long long sF_static[kPw ? 1 : 3 * kTableEntries];
+  extern __shared__ __align__(16) long long sF_dynamic[];
+  long long* const sF = kPw ? sF_dynamic : sF_static;
+  if constexpr (kPw) {
+    for (int i = threadIdx.x; i < P.n_pw * 3 * kTableEntries; i += blockDim.x) sF[i] = table[i];
+    __syncthreads();
+  } else if (!kApprox) {
+    load_table(P, sF);
+  }
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const uint4 p = pts[i];
@@ -31,7 +40,7 @@ __global__ void __launch_bounds__(256) k_project_cert(const uint4* __restrict__ 
         key = make_key((unsigned long long)f.q, p.w);
       }
     } else {
-      const FastFrag f = classify_fast(P, sF, p);
+      const FastFrag f = classify_fast<CertParams, kPw>(P, sF, p);
       if (f.state == kExact) {
         pix = f.pixel;
         key = key_from_fixed(f.a0, f.a1, f.a2, p.w);
