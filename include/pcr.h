@@ -150,7 +150,8 @@ pcr_status pcr_render_atomicmin(pcr_framebuffer* fb, const pcr_point* d_points, 
 /* pcr_render_atomicmin that also adds, to d_counts[0..3] (caller-owned device u64, not cleared), how the
  * EXACT transform's single-precision evaluation handled the points: [0] decided by the first tier (float
  * pixel estimate with its error bound, exact depth code), [1] depth code undecided between two
- * neighbours, [2] sent to the FP64 arbiter, [3] deferred to the second tier (double-float clip values).
+ * neighbours, [2] sent to the FP64 arbiter, [3] deferred to the second tier (double-float clip values; the
+ * points of [1] included).
  * For PIECEWISE depth the points the first tier leaves undecided go to the FP64 arbiter directly ([2] and [3]
  * then count the same points). All four stay 0 when the view is evaluated by the FP64 kernels (transform
  * FP64, or a view outside the single-precision preconditions). A diagnostic of the transform; the framebuffer

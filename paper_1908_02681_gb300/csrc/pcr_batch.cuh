@@ -236,11 +236,7 @@ __global__ void __launch_bounds__(kCertThreads, PCR_BATCH_MIN_BLOCKS) k_batch_pa
           pix = f.pixel;
           key = key_from_fixed(f.a0, f.a1, f.a2, p.w);
           has = f.state == kExact;
-          defer = f.state == kDefer;
-          if (f.state == kAmbiguous) {
-            const unsigned long long klo = f.lo_half ? key - (1ull << 24) : key;
-            defer = klo < stored_key(keys, pix);
-          }
+          defer = f.state >= kAmbiguous;  // undecided pixel, or code undecided between two neighbours: tier 2
         }
         commit_min<kMerge>(has && key < stored_key(keys, pix), pix, key, keys, lane, seg);
         unsigned dummy = 0;
@@ -251,18 +247,9 @@ __global__ void __launch_bounds__(kCertThreads, PCR_BATCH_MIN_BLOCKS) k_batch_pa
         if (valid) {
           const FastFrag f = classify_fast(H, sF, p);
           pix = f.pixel;
-          defer = f.state == kDefer;
-          if ((f.state == kExact) | (f.state == kAmbiguous)) {
-            const unsigned long long qmin = stored_key(keys, pix) >> 24;
-            const unsigned long long qc = code_from_fixed(f.a1, f.a2);
-            const bool amb = f.state == kAmbiguous;
-            accept = in_band(amb && f.lo_half ? qc - 1 : qc, qmin, Pg.v.nq, eps_num, eps_den);
-            if (amb) {
-              const bool other = in_band(f.lo_half ? qc : qc + 1, qmin, Pg.v.nq, eps_num, eps_den);
-              defer = accept != other;
-              accept = accept && !defer;
-            }
-          }
+          defer = f.state >= kAmbiguous;
+          if (f.state == kExact)
+            accept = in_band(code_from_fixed(f.a1, f.a2), stored_key(keys, pix) >> 24, Pg.v.nq, eps_num, eps_den);
         }
         commit_add<kMerge>(accept, pix, p.w, accum, lane, seg);
         defer_points(defer, p, q, qn, lane,

@@ -28,10 +28,11 @@
 // double-float clip values above, whose float roundings are certified, and the definition's IEEE single
 // pixel mapping.
 //
-// A point whose depth code is undecided between two neighbours is sent on only when it could still win
-// its pixel (its smaller candidate key is below the key the framebuffer holds); a point whose cull or
-// pixel tier 2 cannot decide, and those, go through the FP64 definition directly (the arbiter). The
-// output is therefore bit-identical to the FP64 definition.
+// A point whose depth code tier 1 leaves undecided between two neighbours goes to tier 2 too (rare: settling
+// it in tier 1 would cost every point extra work). There, pass 1 sends it on only when its smaller candidate
+// key could still win its pixel, and pass 2 only when the two candidates give different band answers; a point
+// whose cull or pixel tier 2 cannot decide, and those, go through the FP64 definition directly (the arbiter).
+// The output is therefore bit-identical to the FP64 definition.
 #pragma once
 
 #include <cmath>
@@ -581,10 +582,9 @@ __device__ __forceinline__ float rcp_approx(float x) {
 
 // Tier-1 result: state, pixel, and the fixed-point t as three 32-bit words (t * 2^40, low word first).
 struct FastFrag {
-  uint32_t state;  // kCulled, kExact, kAmbiguous (code qc - 1 or qc when lo_half, else qc or qc + 1), kDefer
+  uint32_t state;  // kCulled, kExact, kAmbiguous (code undecided between two neighbours), kDefer
   uint32_t pixel;
   uint32_t a0, a1, a2;
-  bool lo_half;    // kAmbiguous: the fraction is below one half
 };
 
 // Key of the code floor(V / 2^40) (0 <= code < 2^40 - 2): (V >> 16) with the low 24 bits replaced by RGB.
@@ -679,7 +679,6 @@ __device__ __forceinline__ FastFrag classify_fast(const PP& P, const long long* 
   // an undecided code still has two usable candidates.
   const float hD = __fmaf_rn(-kd, s, hd0);
   const bool exact = fabsf(__fsub_rn(frac, 0.5f)) < hD;
-  out.lo_half = frac < 0.5f;
   const bool amb_ok = hD > 0.25f;
 
   // ---- pixel estimate: gx = w (fx - 1/2), gy = w (fy - 1/2) up to the rounding bounds; with wf > 0 (depth_in)
@@ -1072,13 +1071,10 @@ __global__ void __launch_bounds__(kCertThreads, kApprox ? PCR_CERT_APPROX_MIN_BL
         pix = f.pixel;
         key = key_from_fixed(f.a0, f.a1, f.a2, p.w);
         has = f.state == kExact;
-        defer = f.state == kDefer;
-        if (f.state == kAmbiguous) {
-          // candidates qc - 1, qc (lo_half) or qc, qc + 1: only the smaller one can matter
-          const unsigned long long klo = f.lo_half ? key - (1ull << 24) : key;
-          defer = klo < keys[pix];
-          if (kStats) ++c_amb;
-        }
+        // an undecided pixel, or a code undecided between two neighbours (rare: settling it here would cost
+        // every point a predicated key read), goes to tier 2
+        defer = f.state >= kAmbiguous;
+        if (kStats) c_amb += f.state == kAmbiguous;
         if (kStats) {
           c_exact += has;
           c_defer += defer;
@@ -1164,11 +1160,11 @@ __device__ __noinline__ void hq_deferred(const CertParams& P, const long long* s
   if (accept) hq_add(accum, pix, p.w);
 }
 
-// Pass 2 (Section 2.2) with the certified transform, same two tiers and the same point staging as pass 1,
-// one point at a time at 48 registers and 5 blocks per SM (the fastest measured shape: two points per lane
-// with both stored-key reads in flight needs 64 registers and 4 blocks, and ran 1-2 % slower).
+// Pass 2 (Section 2.2) with the certified transform, same two tiers and the same point staging as pass 1, at
+// 64 registers and 4 blocks per SM with both points of a lane classified before their stored-key reads (the
+// fastest measured shape: 1.5 % faster than one point at a time at 48 registers and 5 blocks).
 #ifndef PCR_HQ_MIN_BLOCKS
-#define PCR_HQ_MIN_BLOCKS 5
+#define PCR_HQ_MIN_BLOCKS 4
 #endif
 template <bool kApprox, bool kMerge, bool kRing>
 __global__ void __launch_bounds__(kCertThreads, PCR_HQ_MIN_BLOCKS) k_hq_cert(
@@ -1185,45 +1181,54 @@ __global__ void __launch_bounds__(kCertThreads, PCR_HQ_MIN_BLOCKS) k_hq_cert(
   if (!kApprox) load_table(P, table, sF);
   uint4* q = queue[warp];
   uint32_t qn = 0;
-  // Per point: tier 1 (or the double-float evaluation), the band test against the stored key, the colour
-  // and count additions of an accepted fragment, then the deferral of a point tier 1 could not decide.
-  auto point = [&](const uint4& p, bool valid) {
-    bool defer = false, accept = false;
+  // Double-float mode, per point: the evaluation, the band test against the stored key, the additions.
+  auto point_df = [&](const uint4& p, bool valid) {
+    bool accept = false;
     uint32_t pix = 0;
     if (valid) {
-      if (kApprox) {
-        const CertFrag f = classify_df(P, p);
-        pix = f.pixel;
-        defer = hq_decide(P, f, keys, eps_num, eps_den, &accept);
-      } else {
-        const FastFrag f = classify_fast(P, sF, p);
-        pix = f.pixel;
-        defer = f.state == kDefer;
-        if ((f.state == kExact) | (f.state == kAmbiguous)) {
-          const unsigned long long qmin = stored_key(keys, pix) >> 24;
-          const unsigned long long qc = code_from_fixed(f.a1, f.a2);
-          const bool amb = f.state == kAmbiguous;
-          // an undecided code (candidates qc - 1, qc or qc, qc + 1) is settled here when both candidates
-          // give the same band answer, else the point goes to tier 2
-          accept = in_band(amb && f.lo_half ? qc - 1 : qc, qmin, P.v.nq, eps_num, eps_den);
-          if (amb) {
-            const bool other = in_band(f.lo_half ? qc : qc + 1, qmin, P.v.nq, eps_num, eps_den);
-            defer = accept != other;
-            accept = accept && !defer;
-          }
-        }
-      }
+      const CertFrag f = classify_df(P, p);
+      pix = f.pixel;
+      hq_decide(P, f, keys, eps_num, eps_den, &accept);
     }
     commit_add<kMerge>(accept, pix, p.w, accum, lane);
-    if (!kApprox)
-      defer_points(defer, p, q, qn, lane,
-                   [&](const uint4& d) { hq_deferred(P, sF, d, keys, accum, eps_num, eps_den); });
   };
+  // Exact mode, tier 1 of one point: decided (exact code), or deferred to tier 2 (undecided pixel, or a code
+  // undecided between two neighbours: rare, and settling it here would cost every point a second band test).
+  auto frag = [&](const uint4& p, bool valid, bool& exact, bool& defer, uint32_t& pix, unsigned long long& qc) {
+    exact = false;
+    defer = false;
+    pix = 0;
+    qc = 0;
+    if (valid) {
+      const FastFrag f = classify_fast(P, sF, p);
+      pix = f.pixel;
+      exact = f.state == kExact;
+      defer = f.state >= kAmbiguous;
+      qc = code_from_fixed(f.a1, f.a2);
+    }
+  };
+  // Both points of the lane's tile are classified first, so that their two stored-key reads are in flight
+  // together; then the band tests, the additions, the deferrals.
   const bool done = stream_tiles<kRing>(pts, n, ring[warp], bars[warp], lane,
-                                 [&](const uint4& p0, bool v0, const uint4& p1, bool v1) {
-                                   point(p0, v0);
-                                   point(p1, v1);
-                                 });
+                                        [&](const uint4& p0, bool v0, const uint4& p1, bool v1) {
+    if constexpr (kApprox) {
+      point_df(p0, v0);
+      point_df(p1, v1);
+    } else {
+      bool e0, e1, d0, d1;
+      uint32_t x0, x1;
+      unsigned long long q0, q1;
+      frag(p0, v0, e0, d0, x0, q0);
+      frag(p1, v1, e1, d1, x1, q1);
+      const unsigned long long m0 = e0 ? stored_key(keys, x0) >> 24 : 0ull;
+      const unsigned long long m1 = e1 ? stored_key(keys, x1) >> 24 : 0ull;
+      commit_add<kMerge>(e0 && in_band(q0, m0, P.v.nq, eps_num, eps_den), x0, p0.w, accum, lane);
+      commit_add<kMerge>(e1 && in_band(q1, m1, P.v.nq, eps_num, eps_den), x1, p1.w, accum, lane);
+      auto tier2 = [&](const uint4& d) { hq_deferred(P, sF, d, keys, accum, eps_num, eps_den); };
+      defer_points(d0, p0, q, qn, lane, tier2);
+      defer_points(d1, p1, q, qn, lane, tier2);
+    }
+  });
   if (!done && lane == 0) atomicOr(status, kStatusTimeout);
   if (!kApprox && lane < qn) hq_deferred(P, sF, q[lane], keys, accum, eps_num, eps_den);
 }
