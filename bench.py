@@ -212,6 +212,10 @@ def _config(wl, args, n, world=1):
     return {"workload": wl["desc"], "points": n, "width": view.width, "height": view.height,
             "transform": args.transform,
             "step": "atomicMin pass + basic resolve + HQ band pass + HQ resolve with clear",
+            "band_filter": "on: pass 1 records the points that may be in the eps band, pass 2 skips the others "
+                           "(exact)" if getattr(args, "band_filter", False) else "off",
+            "band_bounds": "on: pass 2 tests codes against per-pixel bounds from one extra kernel (exact)"
+                           if getattr(args, "band_bounds", False) else "off",
             "l2": f"inputs {wl['n'] * 16 / 1e9:.2f} GB > 129 MB L2: no flush between steps",
             "parallelism": "replicas" if world > 1 else "single GPU"}
 
@@ -335,6 +339,10 @@ def run_ours(args, wl):
     img_hq = torch.empty(npx, dtype=torch.int32, device=dev)
     fb = pcr.pcr_create_framebuffer(W, H, pcr.PCR_FB_HQ)
     eps = (1, 100)
+    # --band-filter: pass 1 records which points may still be in the HQ band, pass 2 skips the others (exact;
+    # faster for shuffled clouds, slower for scan-ordered ones)
+    pcr.pcr_set_tuning(fb, 0, 8, 0, band_filter=1 if args.band_filter else 0, band_eps=eps,
+                       band_bounds=1 if args.band_bounds else 0)
 
     names = ["raster_atomicmin", "resolve_basic", "hq_accumulate", "resolve_hq"]
 
@@ -823,6 +831,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="default run: skip the batched sub-result")
+    ap.add_argument("--band-filter", action="store_true",
+                    help="pass 1 records which points may be in the HQ band; pass 2 skips the others")
+    ap.add_argument("--band-bounds", action="store_true",
+                    help="pass 2 tests codes against per-pixel bounds computed by one extra kernel")
     ap.add_argument("--no-serving", action="store_true", help="default run: skip the serving sub-result")
     ap.add_argument("--cpu-sample", type=int, default=100_000_000)
     ap.add_argument("--reference-sample", type=int, default=0,

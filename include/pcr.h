@@ -105,13 +105,33 @@ typedef struct {
                                loads, one tile ahead; 1 bulk copies (cp.async.bulk) into a two-stage
                                shared-memory ring whose waits are bounded (a wait that gives up sets the
                                timeout status, see pcr_get_device_status) */
+  int32_t band_filter;      /* 1: pcr_render_atomicmin on an HQ framebuffer (exact transform, LINEAR or METRIC)
+                               also records which points may still be in the HQ band of eps <=
+                               band_eps_num / band_eps_den, and a following pcr_hq_accumulate of the same
+                               points (pointer, count, view; the points unchanged in between) with such an eps
+                               skips the others. The records are exact: a stored key only decreases, so a point
+                               whose code is already beyond the band of the key its pixel held can never be
+                               accepted. pcr_render_hq_splat and pcr_render_frame_host do the same between
+                               their two passes. 0 (default): nothing is recorded. It pays off when points come
+                               in random order (pass 2 about 20 % faster), not in scan order, where pass 1's
+                               extra work outweighs it; the autotuner tries both. The first
+                               recording of n points allocates n / 8 bytes of device memory (not during stream
+                               capture, where nothing is recorded); a clear drops the record. */
+  uint32_t band_eps_num, band_eps_den; /* eps of the records (default 1 / 100); band_eps_den in 1..2^20 */
+  int32_t band_bounds;      /* 1: pass 2 with the exact transform first turns each pixel's qmin into its accept
+                               bounds {qmin, qmin + floor(eps_num * (qmin + Nq) / eps_den)} (one more kernel,
+                               24 B per pixel) and tests each decided code q by lo <= q <= hi, where the host
+                               finds eps_num * (2^40 + Nq) + eps_den * 2^40 <= 2^64 (the same decision as the
+                               band test of pcr_render_hq_splat then); 0 (default): the band test on the stored
+                               key. Faster for points in random order (pass 2 about 5 %), slower by the extra
+                               kernel in scan order; the autotuner tries both. */
 } pcr_tuning;
 
 /* Framebuffer flags. */
-#define PCR_FB_HQ 1u /* also allocate the 16 B/pixel HQ accumulation buffer (needed by pcr_render_hq_splat) */
+#define PCR_FB_HQ 1u /* also allocate the HQ buffers, 32 B/pixel (needed by pcr_render_hq_splat) */
 
 /* Allocates a width x height framebuffer on the current device (keys: 8 B/pixel; with PCR_FB_HQ also
- * sums: 16 B/pixel; plus a 96 KB device copy of the depth tables of the view last rendered, re-uploaded on
+ * sums: 16 B/pixel, and pass 2's per-pixel band bounds: 16 B/pixel; plus a 96 KB device copy of the depth tables of the view last rendered, re-uploaded on
  * the render call's stream when the view changes) and clears it (synchronously). width, height in
  * 1..16384. */
 pcr_status pcr_create_framebuffer(int32_t width, int32_t height, uint32_t flags, pcr_framebuffer** out);
@@ -127,7 +147,8 @@ pcr_status pcr_set_tuning(pcr_framebuffer* fb, const pcr_tuning* tuning);
 pcr_status pcr_get_tuning(const pcr_framebuffer* fb, pcr_tuning* tuning);
 
 /* Autotuner: renders one frame of (d_points, n, view) on fb for every candidate tuning (same-pixel merging
- * on and off, both stagings, 2 / 4 / 6 / 8 blocks per SM), times the point passes with CUDA events on `stream` (pass 1,
+ * on and off, both stagings, 2 / 4 / 6 / 8 blocks per SM, and for HQ framebuffers band records with eps 1/100
+ * and pass 2's per-pixel bounds, each on and off), times the point passes with CUDA events on `stream` (pass 1,
  * plus pass 2 with eps 1/100 for HQ framebuffers; best of two runs), and keeps the fastest in fb. Writes it
  * to *best when best is not NULL. Clears fb before every run and at the end; synchronises `stream`.
  * Arguments as for pcr_render_atomicmin; n must be > 0. */
@@ -177,7 +198,8 @@ pcr_status pcr_project_points(const pcr_point* d_points, uint64_t n, const pcr_v
  * linear depth at most (1 + eps_num / eps_den) times the closest (eps = 1/100 in the paper).
  * Requirements: fb created with PCR_FB_HQ, and cleared; depth_mode LINEAR or METRIC; 1 <= eps_den <= 2^20;
  * eps_num * (2^40 + Nq) < 2^64. Colour sums are u32 per channel: valid while every pixel gets at most 2^24
- * contributing fragments (checked by the HQ resolve, reported as PCR_ERR_OVERFLOW). */
+ * contributing fragments (checked by the HQ resolve, reported as PCR_ERR_OVERFLOW). pcr_tuning.band_bounds
+ * selects how pass 2 evaluates the test; the result is the same. */
 pcr_status pcr_render_hq_splat(pcr_framebuffer* fb, const pcr_point* d_points, uint64_t n, const pcr_view* view,
                                uint32_t eps_num, uint32_t eps_den, pcr_stream_t stream);
 

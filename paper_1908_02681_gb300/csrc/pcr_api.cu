@@ -23,6 +23,7 @@ struct pcr_framebuffer {
   int device;
   unsigned long long* keys;  // width * height
   ulonglong2* accum;         // width * height (HQ only)
+  ulonglong2* bounds;        // width * height (HQ only): pass 2's per-pixel accept bounds (pcr::k_band_bounds)
   uint32_t* status;          // device status word
   pcr::Tuning tuning;        // launch tuning of the point passes
   // device copy of the depth table of the view last rendered with the certified transform (loaded by the
@@ -33,6 +34,15 @@ struct pcr_framebuffer {
   // frames from host memory (pcr_render_frame_host): copy stream and events, created by its first call
   cudaStream_t copy_stream;
   cudaEvent_t copy_events[9];  // [0]: start of the frame on the caller's stream; [1..8]: chunk k landed
+  // band mask (pass 1 -> pass 2, see pcr::BandMask): two words per 64 points, grown on demand; valid for the
+  // points, count, view and eps of the pass 1 that wrote it, until the framebuffer is cleared
+  uint32_t* band_mask;
+  uint64_t band_words;
+  bool band_valid;
+  const void* band_pts;
+  uint64_t band_n;
+  pcr::DevView band_view;
+  uint32_t band_num, band_den;
 };
 
 namespace {
@@ -177,19 +187,82 @@ const long long* fb_table(pcr_framebuffer* fb, const pcr::DevView& dv, int trans
   return fb->d_table;
 }
 
-// Launches pass 1 (atomic minimum) for a validated view.
+// A band mask request for pass 1: on, its eps, and where the launch's first tile sits in the mask (a pass 1
+// over a tile-aligned part of the frame's points).
+struct BandRequest {
+  bool on = false;
+  uint32_t num = 1, den = 100;
+  uint64_t tile_offset = 0;
+};
+
+// Makes the framebuffer's band mask hold `n_total` points (grown with cudaMalloc outside stream capture only);
+// false when it cannot (then pass 1 writes no mask). The mask stops describing any points.
+bool band_reserve(pcr_framebuffer* fb, uint64_t n_total, cudaStream_t s) {
+  fb->band_valid = false;
+  const uint64_t words = 2 * ((n_total + pcr::kTile - 1) / pcr::kTile);
+  if (words <= fb->band_words) return true;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return false;
+  }
+  uint32_t* m = nullptr;
+  if (cudaMalloc(&m, words * sizeof(uint32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (fb->band_mask) {
+    cudaStreamSynchronize(s);  // the old mask may still be read by pass 2 on this stream
+    cudaFree(fb->band_mask);
+  }
+  fb->band_mask = m;
+  fb->band_words = words;
+  return true;
+}
+
+// Whether pass 1 of this view can write a band mask: the exact transform on a LINEAR or METRIC view of an HQ
+// framebuffer.
+bool band_applies(pcr_framebuffer* fb, const pcr::DevView& dv, int transform) {
+  if (!(fb->flags & PCR_FB_HQ) || transform != PCR_TRANSFORM_EXACT) return false;
+  const pcr::CertParams* P = nullptr;
+  return pcr::cached_cert(dv, false, &P) && P->n_pw == 0;
+}
+
+// Launches pass 1 (atomic minimum) for a validated view. band.on: also write the band mask (the caller reserved
+// it and records what it describes).
 pcr_status launch_raster(pcr_framebuffer* fb, const pcr_point* d_points, uint64_t n, const pcr::DevView& dv,
-                         int transform, cudaStream_t s, unsigned long long* stats = nullptr) {
+                         int transform, cudaStream_t s, unsigned long long* stats = nullptr,
+                         const BandRequest& band = BandRequest()) {
   const uint4* pts = reinterpret_cast<const uint4*>(d_points);
   if (transform == PCR_TRANSFORM_FP64) {
     pcr::k_raster_fp64<<<grid_for(n, 256, fb->device, 8), 256, 0, s>>>(pts, n, dv, fb->keys);
     return after_launch("k_raster_fp64");
   }
   const long long* table = fb_table(fb, dv, transform, s);
+  const pcr::BandMask bm{band.on ? fb->band_mask + 2 * band.tile_offset : nullptr, band.num, band.den};
   return pcr::launch_raster_certified(pts, n, dv, transform == PCR_TRANSFORM_DOUBLE_FLOAT, fb->keys, fb->status,
-                                      sm_count(fb->device), s, stats, fb->tuning, table)
+                                      sm_count(fb->device), s, stats, fb->tuning, table, bm)
              ? after_launch("k_raster_certified")
              : fail(PCR_ERR_CUDA, "certified raster launch failed");
+}
+
+// Pass 1 of n points with a band mask for eps num / den when it applies; records what the mask describes.
+pcr_status launch_raster_band(pcr_framebuffer* fb, const pcr_point* d_points, uint64_t n, const pcr::DevView& dv,
+                              int transform, uint32_t num, uint32_t den, cudaStream_t s) {
+  BandRequest band;
+  band.on = band_applies(fb, dv, transform) && band_reserve(fb, n, s);
+  band.num = num;
+  band.den = den;
+  if (pcr_status st = launch_raster(fb, d_points, n, dv, transform, s, nullptr, band)) return st;
+  if (band.on) {
+    fb->band_valid = true;
+    fb->band_pts = d_points;
+    fb->band_n = n;
+    fb->band_view = dv;
+    fb->band_num = num;
+    fb->band_den = den;
+  }
+  return PCR_OK;
 }
 
 pcr_status launch_hq(pcr_framebuffer* fb, const pcr_point* d_points, uint64_t n, const pcr::DevView& dv,
@@ -201,10 +274,15 @@ pcr_status launch_hq(pcr_framebuffer* fb, const pcr_point* d_points, uint64_t n,
     return after_launch("k_hq_fp64");
   }
   const long long* table = fb_table(fb, dv, transform, s);
-  return pcr::launch_hq_certified(pts, n, dv, transform == PCR_TRANSFORM_DOUBLE_FLOAT, fb->keys, acc, eps_num,
-                                  eps_den, fb->status, sm_count(fb->device), s, fb->tuning, table)
-             ? after_launch("k_hq_certified")
-             : fail(PCR_ERR_CUDA, "certified HQ launch failed");
+  // pass 1's band mask, when it describes these points and view and an eps at least this one
+  const bool band = fb->band_valid && transform == PCR_TRANSFORM_EXACT && fb->band_pts == d_points &&
+                    fb->band_n == n && std::memcmp(&fb->band_view, &dv, sizeof(dv)) == 0 &&
+                    (unsigned long long)eps_num * fb->band_den <= (unsigned long long)fb->band_num * eps_den;
+  const int launched = pcr::launch_hq_certified(pts, n, dv, transform == PCR_TRANSFORM_DOUBLE_FLOAT, fb->keys, acc,
+                                                eps_num, eps_den, fb->status, sm_count(fb->device), s, fb->tuning,
+                                                table, band ? fb->band_mask : nullptr,
+                                                fb->tuning.band_bounds ? fb->bounds : nullptr);
+  return after_launch("k_hq_certified", (uint64_t)launched);
 }
 
 }  // namespace
@@ -230,12 +308,14 @@ pcr_status pcr_create_framebuffer(int32_t width, int32_t height, uint32_t flags,
   const uint64_t npx = (uint64_t)width * (uint64_t)height;
   e = cudaMalloc(&fb->keys, npx * sizeof(unsigned long long));
   if (e == cudaSuccess && (flags & PCR_FB_HQ)) e = cudaMalloc(&fb->accum, npx * sizeof(ulonglong2));
+  if (e == cudaSuccess && (flags & PCR_FB_HQ)) e = cudaMalloc(&fb->bounds, npx * sizeof(ulonglong2));
   if (e == cudaSuccess) e = cudaMalloc(&fb->status, 256);
   if (e == cudaSuccess) e = cudaMalloc(&fb->d_table, pcr::kMaxRanges * sizeof(pcr::CertParams::F));
   if (e != cudaSuccess) {
     cudaGetLastError();
     cudaFree(fb->keys);
     cudaFree(fb->accum);
+    cudaFree(fb->bounds);
     cudaFree(fb->status);
     cudaFree(fb->d_table);
     delete fb;
@@ -266,8 +346,10 @@ pcr_status pcr_destroy_framebuffer(pcr_framebuffer* fb) {
   cudaDeviceSynchronize();
   cudaFree(fb->keys);
   cudaFree(fb->accum);
+  cudaFree(fb->bounds);
   cudaFree(fb->status);
   cudaFree(fb->d_table);
+  cudaFree(fb->band_mask);
   if (fb->copy_stream) {
     cudaStreamDestroy(fb->copy_stream);
     for (cudaEvent_t e : fb->copy_events) cudaEventDestroy(e);
@@ -287,9 +369,17 @@ pcr_status pcr_set_tuning(pcr_framebuffer* fb, const pcr_tuning* tuning) {
     return fail(PCR_ERR_INVALID_ARG, "merge_same_pixel must be 0 or 1");
   if (tuning->blocks_per_sm < 1 || tuning->blocks_per_sm > 32) return fail(PCR_ERR_INVALID_ARG, "blocks_per_sm must be in 1..32");
   if (tuning->staging != 0 && tuning->staging != 1) return fail(PCR_ERR_INVALID_ARG, "staging must be 0 or 1");
+  if (tuning->band_filter != 0 && tuning->band_filter != 1) return fail(PCR_ERR_INVALID_ARG, "band_filter must be 0 or 1");
+  if (tuning->band_eps_den == 0 || tuning->band_eps_den > (1u << 20))
+    return fail(PCR_ERR_INVALID_ARG, "band_eps_den must be in 1..2^20");
   fb->tuning.merge = tuning->merge_same_pixel;
   fb->tuning.blocks_per_sm = tuning->blocks_per_sm;
   fb->tuning.staging = tuning->staging;
+  if (tuning->band_bounds != 0 && tuning->band_bounds != 1) return fail(PCR_ERR_INVALID_ARG, "band_bounds must be 0 or 1");
+  fb->tuning.band_filter = tuning->band_filter;
+  fb->tuning.band_bounds = tuning->band_bounds;
+  fb->tuning.band_num = tuning->band_eps_num;
+  fb->tuning.band_den = tuning->band_eps_den;
   return PCR_OK;
 }
 
@@ -299,6 +389,10 @@ pcr_status pcr_get_tuning(const pcr_framebuffer* fb, pcr_tuning* tuning) {
   tuning->merge_same_pixel = fb->tuning.merge;
   tuning->blocks_per_sm = fb->tuning.blocks_per_sm;
   tuning->staging = fb->tuning.staging;
+  tuning->band_filter = fb->tuning.band_filter;
+  tuning->band_bounds = fb->tuning.band_bounds;
+  tuning->band_eps_num = fb->tuning.band_num;
+  tuning->band_eps_den = fb->tuning.band_den;
   return PCR_OK;
 }
 
@@ -320,15 +414,20 @@ pcr_status pcr_autotune(pcr_framebuffer* fb, const pcr_point* d_points, uint64_t
   pcr::Tuning best_t = saved;
   float best_ms = 3.0e38f;
   pcr_status st = PCR_OK;
-  for (int cand = 0; cand < 16 && st == PCR_OK; ++cand) {
+  for (int cand = 0; cand < (hq ? 64 : 16) && st == PCR_OK; ++cand) {
     fb->tuning.merge = cand & 1;
     fb->tuning.staging = (cand >> 1) & 1;
-    fb->tuning.blocks_per_sm = 2 + 2 * (cand >> 2);  // 2, 4, 6, 8
+    fb->tuning.blocks_per_sm = 2 + 2 * ((cand >> 2) & 3);  // 2, 4, 6, 8
+    fb->tuning.band_filter = (cand >> 4) & 1;               // HQ: band records (eps 1 / 100) on and off
+    fb->tuning.band_bounds = cand >> 5;                     // HQ: pass 2's per-pixel bounds on and off
+    fb->tuning.band_num = 1;
+    fb->tuning.band_den = 100;
     float run_best = 3.0e38f;
     for (int rep = 0; rep < 2 && st == PCR_OK; ++rep) {
       if ((st = pcr_clear(fb, stream)) != PCR_OK) break;
       cudaEventRecord(e0, s);
-      st = launch_raster(fb, d_points, n, dv, view->transform, s);
+      st = hq && fb->tuning.band_filter ? launch_raster_band(fb, d_points, n, dv, view->transform, 1, 100, s)
+                                        : launch_raster(fb, d_points, n, dv, view->transform, s);
       if (st == PCR_OK && hq) st = launch_hq(fb, d_points, n, dv, view->transform, 1, 100, s);
       cudaEventRecord(e1, s);
       if (cudaEventSynchronize(e1) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "autotune timing");
@@ -354,6 +453,10 @@ pcr_status pcr_autotune(pcr_framebuffer* fb, const pcr_point* d_points, uint64_t
     best->merge_same_pixel = fb->tuning.merge;
     best->blocks_per_sm = fb->tuning.blocks_per_sm;
     best->staging = fb->tuning.staging;
+    best->band_filter = fb->tuning.band_filter;
+    best->band_bounds = fb->tuning.band_bounds;
+    best->band_eps_num = fb->tuning.band_num;
+    best->band_eps_den = fb->tuning.band_den;
   }
   return st;
 }
@@ -368,6 +471,7 @@ pcr_status pcr_framebuffer_info(const pcr_framebuffer* fb, int32_t* width, int32
 
 pcr_status pcr_clear(pcr_framebuffer* fb, pcr_stream_t stream) {
   if (pcr_status st = check_fb(fb)) return st;
+  fb->band_valid = false;
   const uint64_t npx = (uint64_t)fb->width * fb->height;
   pcr::k_clear<<<grid_for(npx / 2 + 1, 256, fb->device, 4), 256, 0, (cudaStream_t)stream>>>(fb->keys, fb->accum, npx);
   return after_launch("k_clear");
@@ -380,6 +484,9 @@ pcr_status pcr_render_atomicmin(pcr_framebuffer* fb, const pcr_point* d_points, 
   pcr::DevView dv;
   if (pcr_status st = make_dev_view(view, fb->width, fb->height, &dv)) return st;
   if (n == 0) return PCR_OK;
+  if (fb->tuning.band_filter)
+    return launch_raster_band(fb, d_points, n, dv, view->transform, fb->tuning.band_num, fb->tuning.band_den,
+                              (cudaStream_t)stream);
   return launch_raster(fb, d_points, n, dv, view->transform, (cudaStream_t)stream);
 }
 
@@ -462,7 +569,10 @@ pcr_status pcr_render_hq_splat(pcr_framebuffer* fb, const pcr_point* d_points, u
   if (pcr_status st = check_hq(fb, d_points, n, view, eps_num, eps_den, &dv)) return st;
   if (n == 0) return PCR_OK;
   const cudaStream_t s = (cudaStream_t)stream;
-  if (pcr_status st = launch_raster(fb, d_points, n, dv, view->transform, s)) return st;
+  const pcr_status st = fb->tuning.band_filter ? launch_raster_band(fb, d_points, n, dv, view->transform, eps_num,
+                                                                    eps_den, s)
+                                               : launch_raster(fb, d_points, n, dv, view->transform, s);
+  if (st != PCR_OK) return st;
   return launch_hq(fb, d_points, n, dv, view->transform, eps_num, eps_den, s);
 }
 
@@ -480,6 +590,7 @@ pcr_status pcr_resolve(pcr_framebuffer* fb, uint32_t* d_rgba_out, uint32_t backg
   if (!d_rgba_out) return fail(PCR_ERR_INVALID_ARG, "d_rgba_out is NULL");
   if (!(fb->flags & PCR_FB_HQ)) return pcr_resolve_basic(fb, d_rgba_out, background_rgba, clear_after, stream);
   const uint64_t npx = (uint64_t)fb->width * fb->height;
+  if (clear_after) fb->band_valid = false;
   pcr::k_resolve_hq<<<grid_for(npx, 256, fb->device, 4), 256, 0, (cudaStream_t)stream>>>(
       fb->accum, fb->keys, d_rgba_out, npx, background_rgba, clear_after != 0, fb->status);
   return after_launch("k_resolve_hq");
@@ -490,6 +601,7 @@ pcr_status pcr_resolve_basic(pcr_framebuffer* fb, uint32_t* d_rgba_out, uint32_t
   if (pcr_status st = check_fb(fb)) return st;
   if (!d_rgba_out) return fail(PCR_ERR_INVALID_ARG, "d_rgba_out is NULL");
   const uint64_t npx = (uint64_t)fb->width * fb->height;
+  if (clear_after) fb->band_valid = false;
   pcr::k_resolve_basic<<<grid_for(npx, 256, fb->device, 4), 256, 0, (cudaStream_t)stream>>>(
       fb->keys, fb->accum, d_rgba_out, npx, background_rgba, clear_after != 0);
   return after_launch("k_resolve_basic");
@@ -550,17 +662,32 @@ pcr_status pcr_render_frame_host(pcr_framebuffer* fb, const pcr_point* h_points,
   e = cudaEventRecord(fb->copy_events[0], s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(fb->copy_stream, fb->copy_events[0], 0);
   if (e != cudaSuccess) return cuda_fail(e, "frame start");
-  // up to 8 chunks: pass 1 of chunk k runs while chunk k + 1 is still being copied
+  // up to 8 chunks: pass 1 of chunk k runs while chunk k + 1 is still being copied. Chunk bounds are multiples
+  // of 64 points, so that each chunk's band mask (HQ frames) is its part of the frame's mask.
   const uint64_t chunks = n < (8ull << 20) ? 1 : 8;
+  BandRequest band;
+  band.on = hq && n > 0 && fb->tuning.band_filter && band_applies(fb, dv, view->transform) && band_reserve(fb, n, s);
+  band.num = eps_num;
+  band.den = eps_den;
+  auto bound = [&](uint64_t k) { return k >= chunks ? n : (n * k / chunks) / pcr::kTile * pcr::kTile; };
   for (uint64_t k = 0; k < chunks && n > 0; ++k) {
-    const uint64_t lo = n * k / chunks, hi = n * (k + 1) / chunks;
+    const uint64_t lo = bound(k), hi = bound(k + 1);
     if (hi == lo) continue;
     e = cudaMemcpyAsync(d_points + lo, h_points + lo, (hi - lo) * sizeof(pcr_point), cudaMemcpyHostToDevice,
                         fb->copy_stream);
     if (e == cudaSuccess) e = cudaEventRecord(fb->copy_events[1 + k], fb->copy_stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, fb->copy_events[1 + k], 0);
     if (e != cudaSuccess) return cuda_fail(e, "point upload");
-    if (pcr_status st = launch_raster(fb, d_points + lo, hi - lo, dv, view->transform, s)) return st;
+    band.tile_offset = lo / pcr::kTile;
+    if (pcr_status st = launch_raster(fb, d_points + lo, hi - lo, dv, view->transform, s, nullptr, band)) return st;
+  }
+  if (band.on) {
+    fb->band_valid = true;
+    fb->band_pts = d_points;
+    fb->band_n = n;
+    fb->band_view = dv;
+    fb->band_num = eps_num;
+    fb->band_den = eps_den;
   }
   if (hq && n > 0)
     if (pcr_status st = launch_hq(fb, d_points, n, dv, view->transform, eps_num, eps_den, s)) return st;

@@ -863,8 +863,9 @@ __global__ void k_wait_check(uint32_t* __restrict__ status, uint32_t limit) {
   if (!ring_wait(&bar[0], 0u, limit) && threadIdx.x == 0) atomicOr(status, kStatusTimeout);
 }
 
-// Runs body(p0, valid0, p1, valid1) on every tile of the warp: the lane's two points of the tile; all 32
-// lanes call body together (body may use warp collectives). Returns false when a bounded wait gave up.
+// Runs body(p0, valid0, p1, valid1, tile) on every tile of the warp: the lane's two points of the tile (points
+// tile * 64 + lane and tile * 64 + 32 + lane); all 32 lanes call body together (body may use warp
+// collectives). Returns false when a bounded wait gave up.
 template <typename Body>
 __device__ __forceinline__ bool stream_ring(const uint4* __restrict__ pts, uint64_t n, uint4 (*ring)[kTile],
                                             uint64_t* bar, uint32_t lane, Body&& body) {
@@ -893,7 +894,7 @@ __device__ __forceinline__ bool stream_ring(const uint4* __restrict__ pts, uint6
     }
     phases ^= 1u << s;
     s ^= 1u;
-    body(p0, lane < cnt, p1, lane + 32u < cnt);
+    body(p0, lane < cnt, p1, lane + 32u < cnt, t);
   }
   return true;
 }
@@ -924,7 +925,7 @@ __device__ __forceinline__ bool stream_direct(const uint4* __restrict__ pts, uin
       a0 = ld_stream16(p);
       a1 = ld_stream16(p + 32);
     }
-    body(c0, true, c1, true);
+    body(c0, true, c1, true, t);
   }
   const uint32_t rem = (uint32_t)(n - n_full * kTile);
   if (t == n_full && rem != 0u) {
@@ -932,7 +933,7 @@ __device__ __forceinline__ bool stream_direct(const uint4* __restrict__ pts, uin
     const uint4 z = make_uint4(0u, 0u, 0u, 0u);
     const uint4 c0 = lane < rem ? ld_stream16(b + lane) : z;
     const uint4 c1 = lane + 32u < rem ? ld_stream16(b + lane + 32) : z;
-    body(c0, lane < rem, c1, lane + 32u < rem);
+    body(c0, lane < rem, c1, lane + 32u < rem, n_full);
   }
   return true;
 }
@@ -1030,11 +1031,20 @@ __device__ __forceinline__ void defer_points(bool defer, const uint4& p, uint4* 
 // queued per warp in shared memory and handled 32 at a time by tier 2 and the FP64 arbiter. The points
 // arrive through stream_tiles (direct loads or bulk-copy rings). kPw > 0: PIECEWISE depth (see classify_fast),
 // the ranges' tables in dynamic shared memory (P.n_pw blocks of 3 * kTableEntries entries, from the device table).
-template <bool kApprox, bool kMerge, bool kStats, bool kRing, int kPw>
+// kBand: also writes the band mask for pass 2 (band.mask: two words per tile of 64 points, bit lane of word
+// 2 tile + k for point 64 tile + 32 k + lane): the bit is clear when the point is culled, or when its key is
+// certainly outside the final band of eps = band.num / band.den: eps_den (q - qs) > eps_num (qs + Nq) with qs
+// the code its pixel held when it was read, which is at least the final minimum (a stored key only decreases).
+struct BandMask {
+  uint32_t* mask;
+  uint32_t num, den;
+};
+
+template <bool kApprox, bool kMerge, bool kStats, bool kRing, int kPw, bool kBand = false>
 __global__ void __launch_bounds__(kCertThreads, kApprox ? PCR_CERT_APPROX_MIN_BLOCKS : PCR_CERT_MIN_BLOCKS) k_raster_cert(
     const uint4* __restrict__ pts, uint64_t n, const __grid_constant__ CertParams P,
     unsigned long long* __restrict__ keys, unsigned long long* __restrict__ stats, uint32_t* __restrict__ status,
-    const long long* __restrict__ table) {
+    const long long* __restrict__ table, BandMask band = BandMask{nullptr, 0u, 1u}) {
   __shared__ long long sF_static[kPw ? 1 : 3 * kTableEntries];
   extern __shared__ __align__(16) long long sF_dynamic[];
   __shared__ uint4 queue[kCertWarps][kQueue];
@@ -1056,7 +1066,8 @@ __global__ void __launch_bounds__(kCertThreads, kApprox ? PCR_CERT_APPROX_MIN_BL
   // Per point: tier 1 (or the double-float evaluation), the atomic minimum of a decided fragment whose key
   // is below the stored key, then the deferral of a point tier 1 could not decide. Committing before the
   // deferral keeps the fragment out of the registers that live across the out-of-line tier-2 call.
-  auto point = [&](const uint4& p, bool valid) {
+  // Returns whether pass 2 may need the point (kBand).
+  auto point = [&](const uint4& p, bool valid) -> bool {
     bool defer = false, has = false;
     uint32_t pix = 0;
     unsigned long long key = 0;
@@ -1081,14 +1092,27 @@ __global__ void __launch_bounds__(kCertThreads, kApprox ? PCR_CERT_APPROX_MIN_BL
         }
       }
     }
-    commit_min<kMerge>(has && key < stored_key(keys, pix), pix, key, keys, lane);
+    const unsigned long long sk = has ? stored_key(keys, pix) : 0ull;
+    commit_min<kMerge>(has && key < sk, pix, key, keys, lane);
+    bool need = defer;
+    if constexpr (kBand) {
+      const unsigned long long qk = key >> 24, qs = sk >> 24;
+      const bool out = qk > qs && (unsigned long long)band.den * (qk - qs) > (unsigned long long)band.num * (qs + P.v.nq);
+      need |= has && !out;
+    }
     if (!kApprox)
       defer_points(defer, p, q, qn, lane, [&](const uint4& d) { raster_deferred(P, sF, d, keys, &c_fp64); });
+    return need;
   };
   const bool done = stream_tiles<kRing>(pts, n, ring[warp], bars[warp], lane,
-                                 [&](const uint4& p0, bool v0, const uint4& p1, bool v1) {
-                                   point(p0, v0);
-                                   point(p1, v1);
+                                 [&](const uint4& p0, bool v0, const uint4& p1, bool v1, uint64_t tile) {
+                                   const bool n0 = point(p0, v0);
+                                   const bool n1 = point(p1, v1);
+                                   if constexpr (kBand) {
+                                     const unsigned m0 = __ballot_sync(0xFFFFFFFFu, n0);
+                                     const unsigned m1 = __ballot_sync(0xFFFFFFFFu, n1);
+                                     if (lane == 0) reinterpret_cast<uint2*>(band.mask)[tile] = make_uint2(m0, m1);
+                                   }
                                  });
   if (!done && lane == 0) atomicOr(status, kStatusTimeout);
   if (!kApprox && lane < qn) raster_deferred(P, sF, q[lane], keys, &c_fp64);
@@ -1160,19 +1184,56 @@ __device__ __noinline__ void hq_deferred(const CertParams& P, const long long* s
   if (accept) hq_add(accum, pix, p.w);
 }
 
+// Per-pixel accept bounds of the HQ band (Section 2.2) for one pass 2: bounds[i] = {qmin, qmin + floor(eps_num
+// (qmin + Nq) / eps_den)} with qmin the pixel's stored code. A code q passes in_band against qmin iff
+// bounds.x <= q <= bounds.y whenever eps_num (2^40 + Nq) + eps_den 2^40 <= 2^64 (band_bounds_exact): then
+// eps_den (q - qmin) cannot wrap into the band for q < qmin, and qmin + floor(...) cannot wrap either. One thread
+// per pixel: 8 bytes read, 16 written.
+__global__ void k_band_bounds(const unsigned long long* __restrict__ keys, uint64_t npx, unsigned long long nq,
+                              uint32_t eps_num, uint32_t eps_den, ulonglong2* __restrict__ bounds) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < npx; i += (uint64_t)gridDim.x * blockDim.x) {
+    const unsigned long long qmin = keys[i] >> 24;
+    bounds[i] = make_ulonglong2(qmin, qmin + (unsigned long long)eps_num * (qmin + nq) / eps_den);
+  }
+}
+
+inline bool band_bounds_exact(unsigned long long nq, uint32_t eps_num, uint32_t eps_den) {
+  const unsigned __int128 lhs = (unsigned __int128)eps_num * (((unsigned __int128)1 << 40) + nq) +
+                                ((unsigned __int128)eps_den << 40);
+  return lhs <= ((unsigned __int128)1 << 64);
+}
+
+// A decided code against the band: through the pixel's bounds when they are given, else in_band on its stored key.
+__device__ __forceinline__ bool band_accept(const ulonglong2* bounds, const unsigned long long* keys, uint32_t pix,
+                                            unsigned long long q, unsigned long long nq, uint32_t eps_num,
+                                            uint32_t eps_den) {
+  if (bounds) {
+    const ulonglong2 b = __ldcg(bounds + pix);
+    return q >= b.x && q <= b.y;
+  }
+  return in_band(q, stored_key(keys, pix) >> 24, nq, eps_num, eps_den);
+}
+
 // Pass 2 (Section 2.2) with the certified transform, same two tiers and the same point staging as pass 1, at
 // 64 registers and 4 blocks per SM with both points of a lane classified before their stored-key reads (the
 // fastest measured shape: 1.5 % faster than one point at a time at 48 registers and 5 blocks).
 #ifndef PCR_HQ_MIN_BLOCKS
 #define PCR_HQ_MIN_BLOCKS 4
 #endif
-template <bool kApprox, bool kMerge, bool kRing>
+// kBand: only the points whose bit is set in band_mask (written by pass 1 for the same points and view, see
+// BandMask) can be accepted; each warp appends them to a shared-memory candidate queue and classifies them 32
+// at a time, so the cost follows the points that may be in the band.
+// bounds (exact transform): the pixels' accept bounds from k_band_bounds for this eps, or null (in_band on the
+// stored key). Tier 2 and the arbiter always test against the stored key.
+template <bool kApprox, bool kMerge, bool kRing, bool kBand = false>
 __global__ void __launch_bounds__(kCertThreads, PCR_HQ_MIN_BLOCKS) k_hq_cert(
     const uint4* __restrict__ pts, uint64_t n, const __grid_constant__ CertParams P,
     const unsigned long long* __restrict__ keys, unsigned long long* __restrict__ accum, uint32_t eps_num,
-    uint32_t eps_den, uint32_t* __restrict__ status, const long long* __restrict__ table) {
+    uint32_t eps_den, uint32_t* __restrict__ status, const long long* __restrict__ table,
+    const uint32_t* __restrict__ band_mask = nullptr, const ulonglong2* __restrict__ bounds = nullptr) {
   __shared__ long long sF[3 * kTableEntries];
   __shared__ uint4 queue[kCertWarps][kQueue];
+  __shared__ uint4 cand_queue[kBand ? kCertWarps : 1][kQueue];
   __shared__ __align__(128) uint4 ring[kCertWarps][2][kTile];
   __shared__ __align__(8) uint64_t bars[kCertWarps][2];
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
@@ -1207,11 +1268,42 @@ __global__ void __launch_bounds__(kCertThreads, PCR_HQ_MIN_BLOCKS) k_hq_cert(
       qc = code_from_fixed(f.a1, f.a2);
     }
   };
+  // kBand: one candidate per lane; the point's band test and additions, or its deferral.
+  uint4* cq = cand_queue[kBand ? warp : 0];
+  uint32_t cn = 0;
+  auto candidate = [&](const uint4& p, bool valid) {
+    bool e, d;
+    uint32_t x;
+    unsigned long long qc;
+    frag(p, valid, e, d, x, qc);
+    commit_add<kMerge>(e && band_accept(bounds, keys, x, qc, P.v.nq, eps_num, eps_den), x, p.w, accum, lane);
+    defer_points(d, p, q, qn, lane, [&](const uint4& dd) { hq_deferred(P, sF, dd, keys, accum, eps_num, eps_den); });
+  };
   // Both points of the lane's tile are classified first, so that their two stored-key reads are in flight
   // together; then the band tests, the additions, the deferrals.
   const bool done = stream_tiles<kRing>(pts, n, ring[warp], bars[warp], lane,
-                                        [&](const uint4& p0, bool v0, const uint4& p1, bool v1) {
-    if constexpr (kApprox) {
+                                        [&](const uint4& p0, bool v0, const uint4& p1, bool v1, uint64_t tile) {
+    if constexpr (kBand) {
+      // the tile's two words (the same in every lane); each half's set points are appended to the queue, which
+      // is drained 32 at a time (at most 31 + 32 entries: the queue holds 64)
+      const uint2 bits = reinterpret_cast<const uint2*>(band_mask)[tile];
+      const uint32_t below = (1u << lane) - 1u;
+      auto push = [&](uint32_t word, const uint4& p) {
+        if ((word >> lane) & 1u) cq[cn + __popc(word & below)] = p;
+        cn += __popc(word);
+        __syncwarp();
+        if (cn >= 32u) {
+          cn -= 32u;
+          const uint4 c = cq[cn + lane];
+          __syncwarp();
+          candidate(c, true);
+        }
+      };
+      push(bits.x, p0);
+      push(bits.y, p1);
+      (void)v0;
+      (void)v1;
+    } else if constexpr (kApprox) {
       point_df(p0, v0);
       point_df(p1, v1);
     } else {
@@ -1220,16 +1312,31 @@ __global__ void __launch_bounds__(kCertThreads, PCR_HQ_MIN_BLOCKS) k_hq_cert(
       unsigned long long q0, q1;
       frag(p0, v0, e0, d0, x0, q0);
       frag(p1, v1, e1, d1, x1, q1);
-      const unsigned long long m0 = e0 ? stored_key(keys, x0) >> 24 : 0ull;
-      const unsigned long long m1 = e1 ? stored_key(keys, x1) >> 24 : 0ull;
-      commit_add<kMerge>(e0 && in_band(q0, m0, P.v.nq, eps_num, eps_den), x0, p0.w, accum, lane);
-      commit_add<kMerge>(e1 && in_band(q1, m1, P.v.nq, eps_num, eps_den), x1, p1.w, accum, lane);
+      bool a0, a1;
+      if (bounds) {
+        const ulonglong2 b0 = e0 ? __ldcg(bounds + x0) : make_ulonglong2(1ull, 0ull);
+        const ulonglong2 b1 = e1 ? __ldcg(bounds + x1) : make_ulonglong2(1ull, 0ull);
+        a0 = q0 >= b0.x && q0 <= b0.y;
+        a1 = q1 >= b1.x && q1 <= b1.y;
+      } else {
+        const unsigned long long m0 = e0 ? stored_key(keys, x0) >> 24 : 0ull;
+        const unsigned long long m1 = e1 ? stored_key(keys, x1) >> 24 : 0ull;
+        a0 = e0 && in_band(q0, m0, P.v.nq, eps_num, eps_den);
+        a1 = e1 && in_band(q1, m1, P.v.nq, eps_num, eps_den);
+      }
+      commit_add<kMerge>(a0, x0, p0.w, accum, lane);
+      commit_add<kMerge>(a1, x1, p1.w, accum, lane);
       auto tier2 = [&](const uint4& d) { hq_deferred(P, sF, d, keys, accum, eps_num, eps_den); };
       defer_points(d0, p0, q, qn, lane, tier2);
       defer_points(d1, p1, q, qn, lane, tier2);
     }
   });
   if (!done && lane == 0) atomicOr(status, kStatusTimeout);
+  if constexpr (kBand) {  // the last candidates (fewer than 32)
+    const uint4 c = cq[lane < cn ? lane : 0];
+    __syncwarp();
+    candidate(c, lane < cn);
+  }
   if (!kApprox && lane < qn) hq_deferred(P, sF, q[lane], keys, accum, eps_num, eps_den);
 }
 
@@ -1241,6 +1348,9 @@ struct Tuning {
   int merge = 0;
   int blocks_per_sm = 8;
   int staging = 0;
+  int band_filter = 0;  // pass 1 writes the band mask for eps <= band_num / band_den (see BandMask)
+  uint32_t band_num = 1, band_den = 100;
+  int band_bounds = 0;  // pass 2 tests decided codes against per-pixel bounds (k_band_bounds)
 };
 
 inline unsigned cert_grid(uint64_t n, int sms, int per_sm) {
@@ -1266,11 +1376,11 @@ inline unsigned persistent_grid(int resident, uint64_t n, int sms, int per_sm) {
 
 // table: device copy of P.F (or null: the kernels read it from the parameter block); for PIECEWISE views
 // (P.n_pw > 0) the device copy of all the ranges' tables, required.
-template <bool kApprox, bool kMerge, bool kStats, bool kRing, int kPw>
+template <bool kApprox, bool kMerge, bool kStats, bool kRing, int kPw, bool kBand = false>
 inline void raster_launch5(const uint4* pts, uint64_t n, const CertParams& P, unsigned long long* keys,
                            unsigned long long* stats, uint32_t* status, int sms, int per_sm, cudaStream_t s,
-                           const long long* table) {
-  auto kernel = k_raster_cert<kApprox, kMerge, kStats, kRing, kPw>;
+                           const long long* table, BandMask band = BandMask{nullptr, 0u, 1u}) {
+  auto kernel = k_raster_cert<kApprox, kMerge, kStats, kRing, kPw, kBand>;
   if constexpr (kPw) {
     // the ranges' tables in dynamic shared memory: up to kMaxRanges * 12 KB (opt in above 48 KB once)
     static const bool opted = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1283,17 +1393,26 @@ inline void raster_launch5(const uint4* pts, uint64_t n, const CertParams& P, un
       cudaGetLastError();
       resident = 1;
     }
-    kernel<<<persistent_grid(resident, n, sms, per_sm), kCertThreads, dyn, s>>>(pts, n, P, keys, stats, status, table);
+    kernel<<<persistent_grid(resident, n, sms, per_sm), kCertThreads, dyn, s>>>(pts, n, P, keys, stats, status, table,
+                                                                               band);
   } else {
     static const int resident = resident_blocks(kernel);  // per instantiation
-    kernel<<<persistent_grid(resident, n, sms, per_sm), kCertThreads, 0, s>>>(pts, n, P, keys, stats, status, table);
+    kernel<<<persistent_grid(resident, n, sms, per_sm), kCertThreads, 0, s>>>(pts, n, P, keys, stats, status, table,
+                                                                             band);
   }
 }
 
 template <bool kApprox, bool kMerge, bool kStats, bool kRing>
 inline void raster_launch4(const uint4* pts, uint64_t n, const CertParams& P, unsigned long long* keys,
                            unsigned long long* stats, uint32_t* status, int sms, int per_sm, cudaStream_t s,
-                           const long long* table) {
+                           const long long* table, BandMask band = BandMask{nullptr, 0u, 1u}) {
+  if constexpr (!kApprox && !kStats) {
+    if (band.mask && P.n_pw == 0) {  // also write the band mask for pass 2
+      raster_launch5<false, kMerge, false, kRing, 0, true>(pts, n, P, keys, nullptr, status, sms, per_sm, s, table,
+                                                           band);
+      return;
+    }
+  }
   if (!kApprox && P.n_pw > 2)
     raster_launch5<false, kMerge, kStats, kRing, 2>(pts, n, P, keys, stats, status, sms, per_sm, s, table);
   else if (!kApprox && P.n_pw > 0)
@@ -1306,13 +1425,16 @@ inline void raster_launch4(const uint4* pts, uint64_t n, const CertParams& P, un
 template <bool kApprox, bool kMerge>
 inline void raster_launch(const uint4* pts, uint64_t n, const CertParams& P, unsigned long long* keys,
                           unsigned long long* stats, uint32_t* status, int sms, int per_sm, cudaStream_t s,
-                          const long long* table = nullptr, int staging = 0) {
+                          const long long* table = nullptr, int staging = 0,
+                          BandMask band = BandMask{nullptr, 0u, 1u}) {
   if (stats && !kApprox && !kMerge)
     staging ? raster_launch4<false, false, true, true>(pts, n, P, keys, stats, status, sms, per_sm, s, table)
             : raster_launch4<false, false, true, false>(pts, n, P, keys, stats, status, sms, per_sm, s, table);
   else
-    staging ? raster_launch4<kApprox, kMerge, false, true>(pts, n, P, keys, nullptr, status, sms, per_sm, s, table)
-            : raster_launch4<kApprox, kMerge, false, false>(pts, n, P, keys, nullptr, status, sms, per_sm, s, table);
+    staging ? raster_launch4<kApprox, kMerge, false, true>(pts, n, P, keys, nullptr, status, sms, per_sm, s, table,
+                                                           band)
+            : raster_launch4<kApprox, kMerge, false, false>(pts, n, P, keys, nullptr, status, sms, per_sm, s, table,
+                                                            band);
 }
 
 // The certified constants of a view, prepared on this thread and kept for the next call with the same view
@@ -1341,10 +1463,12 @@ inline bool cached_cert(const DevView& v, bool approximate, const CertParams** o
 inline int table_blocks(const CertParams& P) { return P.n_pw > 0 ? P.n_pw : 1; }
 
 // Pass 1 for a view with n >= 1 points. status: the framebuffer's status word (timeout bit).
+// band (mask non-null): also write the band mask for pass 2 (used only with the exact transform on LINEAR or
+// METRIC views; the caller checks that before relying on it).
 inline bool launch_raster_certified(const uint4* pts, uint64_t n, const DevView& v, bool approximate,
                                     unsigned long long* keys, uint32_t* status, int sms, cudaStream_t s,
                                     unsigned long long* stats = nullptr, const Tuning& t = Tuning(),
-                                    const long long* table = nullptr) {
+                                    const long long* table = nullptr, BandMask band = BandMask{nullptr, 0u, 1u}) {
   const CertParams* Pp = nullptr;
   const unsigned grid = cert_grid(n, sms, t.blocks_per_sm);
   // PIECEWISE views need the device copy of their tables
@@ -1357,48 +1481,79 @@ inline bool launch_raster_certified(const uint4* pts, uint64_t n, const DevView&
     t.merge ? raster_launch<true, true>(pts, n, *Pp, keys, stats, status, sms, b, s, table, g)
             : raster_launch<true, false>(pts, n, *Pp, keys, stats, status, sms, b, s, table, g);
   else
-    t.merge ? raster_launch<false, true>(pts, n, *Pp, keys, stats, status, sms, b, s, table, g)
-            : raster_launch<false, false>(pts, n, *Pp, keys, stats, status, sms, b, s, table, g);
+    t.merge ? raster_launch<false, true>(pts, n, *Pp, keys, stats, status, sms, b, s, table, g, band)
+            : raster_launch<false, false>(pts, n, *Pp, keys, stats, status, sms, b, s, table, g, band);
   return true;
 }
 
-template <bool kApprox, bool kMerge, bool kRing>
-inline void hq_launch3(const uint4* pts, uint64_t n, const CertParams& P, const unsigned long long* keys,
+template <bool kApprox, bool kMerge, bool kRing, bool kBand = false>
+inline void hq_launch4(const uint4* pts, uint64_t n, const CertParams& P, const unsigned long long* keys,
                        unsigned long long* accum, uint32_t eps_num, uint32_t eps_den, uint32_t* status, int sms,
-                       int per_sm, cudaStream_t s, const long long* table) {
-  static const int resident = resident_blocks(k_hq_cert<kApprox, kMerge, kRing>);  // one per instantiation
+                       int per_sm, cudaStream_t s, const long long* table, const uint32_t* band_mask,
+                       const ulonglong2* bounds) {
+  static const int resident = resident_blocks(k_hq_cert<kApprox, kMerge, kRing, kBand>);  // one per instantiation
   const unsigned grid = persistent_grid(resident, n, sms, per_sm);
-  k_hq_cert<kApprox, kMerge, kRing><<<grid, kCertThreads, 0, s>>>(pts, n, P, keys, accum, eps_num, eps_den, status,
-                                                                  table);
+  k_hq_cert<kApprox, kMerge, kRing, kBand><<<grid, kCertThreads, 0, s>>>(pts, n, P, keys, accum, eps_num, eps_den,
+                                                                         status, table, band_mask, bounds);
 }
 
+// band_mask (exact transform only): pass 1's band mask of the same points and view, or null. bounds (exact
+// transform only): the pixels' accept bounds for this eps (k_band_bounds), or null.
 template <bool kApprox, bool kMerge>
 inline void hq_launch(const uint4* pts, uint64_t n, const CertParams& P, const unsigned long long* keys,
                       unsigned long long* accum, uint32_t eps_num, uint32_t eps_den, uint32_t* status, int sms,
-                      int per_sm, cudaStream_t s, const long long* table = nullptr, int staging = 0) {
-  staging ? hq_launch3<kApprox, kMerge, true>(pts, n, P, keys, accum, eps_num, eps_den, status, sms, per_sm, s, table)
-          : hq_launch3<kApprox, kMerge, false>(pts, n, P, keys, accum, eps_num, eps_den, status, sms, per_sm, s, table);
+                      int per_sm, cudaStream_t s, const long long* table = nullptr, int staging = 0,
+                      const uint32_t* band_mask = nullptr, const ulonglong2* bounds = nullptr) {
+  if constexpr (!kApprox) {
+    if (band_mask) {
+      staging ? hq_launch4<false, kMerge, true, true>(pts, n, P, keys, accum, eps_num, eps_den, status, sms, per_sm, s,
+                                                      table, band_mask, bounds)
+              : hq_launch4<false, kMerge, false, true>(pts, n, P, keys, accum, eps_num, eps_den, status, sms, per_sm,
+                                                       s, table, band_mask, bounds);
+      return;
+    }
+  } else {
+    bounds = nullptr;
+  }
+  staging ? hq_launch4<kApprox, kMerge, true>(pts, n, P, keys, accum, eps_num, eps_den, status, sms, per_sm, s, table,
+                                              nullptr, bounds)
+          : hq_launch4<kApprox, kMerge, false>(pts, n, P, keys, accum, eps_num, eps_den, status, sms, per_sm, s, table,
+                                               nullptr, bounds);
 }
 
-// Pass 2 for a view with n >= 1 points. status: the framebuffer's status word (timeout bit).
-inline bool launch_hq_certified(const uint4* pts, uint64_t n, const DevView& v, bool approximate,
-                                const unsigned long long* keys, unsigned long long* accum, uint32_t eps_num,
-                                uint32_t eps_den, uint32_t* status, int sms, cudaStream_t s,
-                                const Tuning& t = Tuning(), const long long* table = nullptr) {
+// Pass 2 for a view with n >= 1 points. status: the framebuffer's status word (timeout bit). band_mask: see
+// hq_launch. bounds_buf: room for the accept bounds of every pixel (npx entries), or null; with the exact
+// transform and band_bounds_exact they are computed (k_band_bounds) and pass 2 tests against them. Returns the
+// number of kernels launched.
+inline int launch_hq_certified(const uint4* pts, uint64_t n, const DevView& v, bool approximate,
+                               const unsigned long long* keys, unsigned long long* accum, uint32_t eps_num,
+                               uint32_t eps_den, uint32_t* status, int sms, cudaStream_t s,
+                               const Tuning& t = Tuning(), const long long* table = nullptr,
+                               const uint32_t* band_mask = nullptr, ulonglong2* bounds_buf = nullptr) {
   const CertParams* Pp = nullptr;
   const unsigned grid = cert_grid(n, sms, t.blocks_per_sm);
   if (!cached_cert(v, approximate, &Pp) || Pp->n_pw > 0) {  // (HQ takes LINEAR or METRIC views only)
     k_hq_fp64<<<grid, 256, 0, s>>>(pts, n, v, keys, accum, eps_num, eps_den);
-    return true;
+    return 1;
   }
   const int b = t.blocks_per_sm, g = t.staging;
-  if (approximate)
+  if (approximate) {
     t.merge ? hq_launch<true, true>(pts, n, *Pp, keys, accum, eps_num, eps_den, status, sms, b, s, table, g)
             : hq_launch<true, false>(pts, n, *Pp, keys, accum, eps_num, eps_den, status, sms, b, s, table, g);
-  else
-    t.merge ? hq_launch<false, true>(pts, n, *Pp, keys, accum, eps_num, eps_den, status, sms, b, s, table, g)
-            : hq_launch<false, false>(pts, n, *Pp, keys, accum, eps_num, eps_den, status, sms, b, s, table, g);
-  return true;
+    return 1;
+  }
+  const ulonglong2* bounds = nullptr;
+  if (bounds_buf && band_bounds_exact(v.nq, eps_num, eps_den)) {
+    const uint64_t npx = (uint64_t)v.width * v.height;
+    const unsigned bgrid = (unsigned)((npx + 255) / 256 < (uint64_t)sms * 8 ? (npx + 255) / 256 : (uint64_t)sms * 8);
+    k_band_bounds<<<bgrid, 256, 0, s>>>(keys, npx, v.nq, eps_num, eps_den, bounds_buf);
+    bounds = bounds_buf;
+  }
+  t.merge ? hq_launch<false, true>(pts, n, *Pp, keys, accum, eps_num, eps_den, status, sms, b, s, table, g,
+                                   band_mask, bounds)
+          : hq_launch<false, false>(pts, n, *Pp, keys, accum, eps_num, eps_den, status, sms, b, s, table, g,
+                                    band_mask, bounds);
+  return bounds ? 2 : 1;
 }
 
 }  // namespace pcr

@@ -38,7 +38,9 @@ class pcr_view(ctypes.Structure):
 
 
 class pcr_tuning(ctypes.Structure):
-    _fields_ = [("merge_same_pixel", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("staging", ctypes.c_int32)]
+    _fields_ = [("merge_same_pixel", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("staging", ctypes.c_int32),
+                ("band_filter", ctypes.c_int32), ("band_eps_num", ctypes.c_uint32), ("band_eps_den", ctypes.c_uint32),
+                ("band_bounds", ctypes.c_int32)]
 
 
 class pcr_batch_tuning(ctypes.Structure):
@@ -230,15 +232,18 @@ def pcr_framebuffer_info(fb: Framebuffer):
 
 
 def _tuning_dict(t: pcr_tuning) -> dict:
-    return {"merge_same_pixel": t.merge_same_pixel, "blocks_per_sm": t.blocks_per_sm, "staging": t.staging}
+    return {"merge_same_pixel": t.merge_same_pixel, "blocks_per_sm": t.blocks_per_sm, "staging": t.staging,
+            "band_filter": t.band_filter, "band_eps": (t.band_eps_num, t.band_eps_den), "band_bounds": t.band_bounds}
 
 
-def pcr_set_tuning(fb: Framebuffer, merge_same_pixel: int | None = 0, blocks_per_sm: int = 8, staging: int = 0):
+def pcr_set_tuning(fb: Framebuffer, merge_same_pixel: int | None = 0, blocks_per_sm: int = 8, staging: int = 0,
+                   band_filter: int = 0, band_eps=(1, 100), band_bounds: int = 0):
     """merge_same_pixel=None restores the library defaults."""
     if merge_same_pixel is None:
         _check(load().pcr_set_tuning(fb.handle, None))
     else:
-        t = pcr_tuning(int(merge_same_pixel), int(blocks_per_sm), int(staging))
+        t = pcr_tuning(int(merge_same_pixel), int(blocks_per_sm), int(staging), int(band_filter), int(band_eps[0]),
+                       int(band_eps[1]), int(band_bounds))
         _check(load().pcr_set_tuning(fb.handle, ctypes.byref(t)))
 
 

@@ -1,0 +1,85 @@
+"""Pass 2's per-pixel accept bounds (Section 2.2 band test): the band test on u64 integers,
+eps_den * (q - qmin) <= eps_num * (qmin + Nq) with both products taken mod 2^64, decides exactly as
+bounds.x <= q <= bounds.y with bounds = {qmin, qmin + floor(eps_num (qmin + Nq) / eps_den)} whenever
+eps_num (2^40 + Nq) + eps_den 2^40 <= 2^64 (the host condition under which the kernels use the bounds), and
+not always beyond it. Python integers, wrap written out, no GPU."""
+from __future__ import annotations
+
+import random
+
+M64 = (1 << 64) - 1
+QMAX = (1 << 40) - 2      # largest depth code
+EMPTY_Q = (1 << 40) - 1   # code of an empty pixel (key all ones >> 24)
+
+
+def in_band_u64(q, qmin, nq, num, den):
+    return (den * ((q - qmin) & M64)) & M64 <= (num * (qmin + nq)) & M64
+
+
+def bounds(qmin, nq, num, den):
+    lo, hi = qmin, qmin + (num * (qmin + nq)) // den
+    assert hi <= M64  # the kernel's u64 sum does not wrap either
+    return lo, hi
+
+
+def condition(nq, num, den):
+    return num * ((1 << 40) + nq) + (den << 40) <= 1 << 64
+
+
+def api_valid(nq, num, den):
+    return 1 <= den <= 1 << 20 and num * ((1 << 40) + nq) < 1 << 64
+
+
+def _cases(rng, nq, num, den, k):
+    for _ in range(k):
+        qmin = rng.choice([0, 1, EMPTY_Q, QMAX, rng.randrange(1 << 40), rng.randrange(1 << 20)])
+        _, hi = bounds(qmin, nq, num, den)
+        near = [qmin, qmin - 1, qmin + 1, hi, hi + 1, hi - 1, 0, QMAX, rng.randrange(1 << 40)]
+        for q in near:
+            if 0 <= q <= QMAX:
+                yield q, qmin
+
+
+def test_bounds_decide_like_the_band_test():
+    rng = random.Random(7)
+    nqs = [0, 1, 1 << 20, 123456789, (1 << 40) - 1]
+    eps = [(1, 100), (1, 1), (0, 1), (3, 7), (1, 1 << 20), ((1 << 20) - 1, 1 << 20), (1000, 3)]
+    n = 0
+    for nq in nqs:
+        for num, den in eps:
+            if not (api_valid(nq, num, den) and condition(nq, num, den)):
+                continue
+            for q, qmin in _cases(rng, nq, num, den, 200):
+                lo, hi = bounds(qmin, nq, num, den)
+                assert in_band_u64(q, qmin, nq, num, den) == (lo <= q <= hi), (q, qmin, nq, num, den)
+                n += 1
+    assert n > 10000
+
+
+def test_largest_eps_inside_the_condition():
+    """The largest eps_num the condition admits for a few (Nq, eps_den): still the same decisions."""
+    rng = random.Random(8)
+    for nq in (0, 1 << 30, (1 << 40) - 1):
+        for den in (1, 2, 100, 1 << 20):
+            num = ((1 << 64) - (den << 40)) // ((1 << 40) + nq)
+            assert condition(nq, num, den) and not condition(nq, num + 1, den)
+            if not api_valid(nq, num, den):
+                continue
+            for q, qmin in _cases(rng, nq, num, den, 300):
+                lo, hi = bounds(qmin, nq, num, den)
+                assert in_band_u64(q, qmin, nq, num, den) == (lo <= q <= hi), (q, qmin, nq, num, den)
+
+
+def test_beyond_the_condition_the_wrap_accepts_nearer_codes():
+    """Outside the condition (a valid eps for the API), the u64 test accepts some q < qmin: the bounds would
+    not, which is why the kernels fall back to the stored-key test there."""
+    nq, den = 0, 2
+    num = (1 << 24) - 1
+    assert api_valid(nq, num, den) and not condition(nq, num, den)
+    qmin = QMAX
+    # den * (qmin - q) = 2^40 + 2^25: the wrapped left side 2^64 - 2^40 - 2^25 is below
+    # eps_num * qmin = 2^64 - 2^40 - 2^25 + 2
+    q = qmin - (1 << 39) - (1 << 24)
+    assert in_band_u64(q, qmin, nq, num, den)
+    lo, hi = bounds(qmin, nq, num, den)
+    assert not (lo <= q <= hi)

@@ -205,6 +205,7 @@ def test_single_view_autotune(gpu):
     dev = _dev(pts)
     best = gpu.pcr_autotune(fb, dev, view)
     assert best["merge_same_pixel"] in (0, 1) and best["staging"] in (0, 1) and best["blocks_per_sm"] in (2, 4, 6, 8)
+    assert best["band_filter"] in (0, 1) and best["band_eps"] == (1, 100) and best["band_bounds"] in (0, 1)
     assert gpu.pcr_get_tuning(fb) == best
     keys, acc = gpu.pcr_framebuffer_keys(fb)
     assert np.all(gpu.keys_to_numpy(keys) == oracle.EMPTY)  # cleared at the end

@@ -289,7 +289,8 @@ def test_tuning_does_not_change_results(gpu, merge, blocks, staging):
     view = scenes.lidar_1km_view(800, 450)
     fb = gpu.pcr_create_framebuffer(view.width, view.height, gpu.PCR_FB_HQ)
     gpu.pcr_set_tuning(fb, merge, blocks, staging)
-    assert gpu.pcr_get_tuning(fb) == {"merge_same_pixel": merge, "blocks_per_sm": blocks, "staging": staging}
+    assert gpu.pcr_get_tuning(fb) == {"merge_same_pixel": merge, "blocks_per_sm": blocks, "staging": staging,
+                                      "band_filter": 0, "band_eps": (1, 100), "band_bounds": 0}
     gpu.pcr_render_hq_splat(fb, _dev(pts), view)
     keys, acc = gpu.pcr_framebuffer_keys(fb)
     ref = oracle.render_atomicmin(pts, view)
