@@ -1188,12 +1188,37 @@ __device__ __noinline__ void hq_deferred(const CertParams& P, const long long* s
 // (qmin + Nq) / eps_den)} with qmin the pixel's stored code. A code q passes in_band against qmin iff
 // bounds.x <= q <= bounds.y whenever eps_num (2^40 + Nq) + eps_den 2^40 <= 2^64 (band_bounds_exact): then
 // eps_den (q - qmin) cannot wrap into the band for q < qmin, and qmin + floor(...) cannot wrap either. One thread
-// per pixel: 8 bytes read, 16 written.
+// per pixel: 8 bytes read, 16 written. The division by eps_den is a multiplication by its invariant-divisor
+// magic number (DivMagic).
+struct DivMagic {
+  unsigned long long m;
+  uint32_t sh1, sh2;
+};
+
+// Exact unsigned 64-bit division by an invariant d >= 1 (Granlund and Montgomery, "Division by invariant integers
+// using multiplication", 1994, unsigned case with N = 64): with l = ceil(log2 d), m = floor(2^64 (2^l - d) / d)
+// + 1 < 2^64, t = floor(m n / 2^64): floor(n / d) = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0) for every
+// 0 <= n < 2^64.
+inline DivMagic div_magic(uint32_t d) {
+  uint32_t l = 0;
+  while (l < 32 && (1ull << l) < d) ++l;
+  DivMagic r;
+  r.m = (unsigned long long)((((unsigned __int128)((1ull << l) - d)) << 64) / d) + 1ull;
+  r.sh1 = l < 1 ? l : 1;
+  r.sh2 = l > 1 ? l - 1 : 0;
+  return r;
+}
+
+__device__ __forceinline__ unsigned long long div_by(unsigned long long n, const DivMagic& D) {
+  const unsigned long long t = __umul64hi(D.m, n);
+  return (t + ((n - t) >> D.sh1)) >> D.sh2;
+}
+
 __global__ void k_band_bounds(const unsigned long long* __restrict__ keys, uint64_t npx, unsigned long long nq,
-                              uint32_t eps_num, uint32_t eps_den, ulonglong2* __restrict__ bounds) {
+                              uint32_t eps_num, DivMagic D, ulonglong2* __restrict__ bounds) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < npx; i += (uint64_t)gridDim.x * blockDim.x) {
     const unsigned long long qmin = keys[i] >> 24;
-    bounds[i] = make_ulonglong2(qmin, qmin + (unsigned long long)eps_num * (qmin + nq) / eps_den);
+    bounds[i] = make_ulonglong2(qmin, qmin + div_by((unsigned long long)eps_num * (qmin + nq), D));
   }
 }
 
@@ -1546,7 +1571,7 @@ inline int launch_hq_certified(const uint4* pts, uint64_t n, const DevView& v, b
   if (bounds_buf && band_bounds_exact(v.nq, eps_num, eps_den)) {
     const uint64_t npx = (uint64_t)v.width * v.height;
     const unsigned bgrid = (unsigned)((npx + 255) / 256 < (uint64_t)sms * 8 ? (npx + 255) / 256 : (uint64_t)sms * 8);
-    k_band_bounds<<<bgrid, 256, 0, s>>>(keys, npx, v.nq, eps_num, eps_den, bounds_buf);
+    k_band_bounds<<<bgrid, 256, 0, s>>>(keys, npx, v.nq, eps_num, div_magic(eps_den), bounds_buf);
     bounds = bounds_buf;
   }
   t.merge ? hq_launch<false, true>(pts, n, *Pp, keys, accum, eps_num, eps_den, status, sms, b, s, table, g,

@@ -83,3 +83,35 @@ def test_beyond_the_condition_the_wrap_accepts_nearer_codes():
     assert in_band_u64(q, qmin, nq, num, den)
     lo, hi = bounds(qmin, nq, num, den)
     assert not (lo <= q <= hi)
+
+
+def div_magic(d):
+    """k_band_bounds' invariant-divisor constants (Granlund and Montgomery 1994, unsigned, N = 64)."""
+    l = 0
+    while (1 << l) < d:
+        l += 1
+    m = (((1 << l) - d) << 64) // d + 1
+    assert m < 1 << 64
+    return m, min(l, 1), max(l - 1, 0)
+
+
+def div_by(n, magic):
+    m, sh1, sh2 = magic
+    t = (m * n) >> 64
+    return ((t + (((n - t) & M64) >> sh1)) & M64) >> sh2
+
+
+def test_invariant_divisor_division_is_exact():
+    """floor(n / d) for every divisor the API admits (1..2^20), sampled, and n at the ends of the u64 range,
+    near multiples of d and at random."""
+    rng = random.Random(9)
+    ds = list(range(1, 300)) + [1 << k for k in range(21)] + [(1 << k) + 1 for k in range(1, 20)] + \
+        [(1 << k) - 1 for k in range(2, 21)] + [rng.randrange(1, (1 << 20) + 1) for _ in range(300)]
+    for d in ds:
+        mg = div_magic(d)
+        ns = [0, 1, d - 1, d, d + 1, M64, M64 - 1, M64 - d, (M64 // d) * d, (M64 // d) * d - 1]
+        ns += [rng.randrange(1 << 64) for _ in range(20)]
+        ns += [k * d + r for k in (rng.randrange(1 << 40), rng.randrange(1 << 60)) for r in (0, d - 1)]
+        for n in ns:
+            n &= M64
+            assert div_by(n, mg) == n // d, (n, d)

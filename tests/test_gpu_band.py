@@ -124,13 +124,14 @@ def test_frame_from_host_buffers_with_records(gpu):
 
 
 @pytest.mark.parametrize("bounds", [0, 1])
-@pytest.mark.parametrize("eps", [(1, 100), ((1 << 24) - 2, 2), ((1 << 24) - 1, 2)])
+@pytest.mark.parametrize("eps", [(1, 100), (3, 7), (1, 1 << 20), (5, 3), ((1 << 24) - 2, 2), ((1 << 24) - 1, 2)])
 def test_band_bounds_and_their_limit(gpu, eps, bounds):
     """With band_bounds, pass 2 tests decided codes against per-pixel bounds {qmin, qmin + floor(eps_num (qmin +
-    Nq) / eps_den)} while eps_num (2^40 + Nq) + eps_den 2^40 <= 2^64, and against the stored key beyond (METRIC view, Nq = 0:
-    (2^24 - 2) / 2 is the last eps inside, (2^24 - 1) / 2 the first outside). Points of another cloud against
-    the minima: where the minimum is the empty code, the u64 test of the largest eps accepts every point (its
-    left side wraps), the bounds would not; the sums must equal the oracle's in all three."""
+    Nq) / eps_den)} while eps_num (2^40 + Nq) + eps_den 2^40 <= 2^64, and against the stored key beyond (METRIC
+    view, Nq = 0: (2^24 - 2) / 2 is the last eps inside, (2^24 - 1) / 2 the first outside; the others take the
+    invariant-divisor division at several divisors). Points of another cloud against the minima: where the
+    minimum is the empty code, the u64 test of the largest eps accepts every point (its left side wraps), the
+    bounds would not; the sums must equal the oracle's in every case."""
     from tests.helpers import RawView
     a = scenes.lidar(1_000_003, 85)
     b = scenes.lidar(1_000_003, 86)

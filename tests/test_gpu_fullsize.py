@@ -109,3 +109,31 @@ def test_batched_64_views_20m_sampled(gpu):
         batch.close()
         for fb in fbs:
             fb.close()
+
+
+@pytest.mark.parametrize("band_filter,band_bounds", [(0, 1), (1, 1)])
+def test_lidar_100m_hq_random_order_options(gpu, lidar100m, band_filter, band_bounds):
+    """The HQ frame at full size with pass 2's per-pixel band bounds (band_bounds) and pass 1's band records
+    (band_filter): sums, counts and the HQ image exact, twice on the same framebuffer."""
+    import torch
+    pts = lidar100m
+    view = scenes.lidar_1km_view()
+    W, H = view.width, view.height
+    dev = torch.from_numpy(pts.view(np.int32)).cuda()
+    fb = gpu.pcr_create_framebuffer(W, H, gpu.PCR_FB_HQ)
+    gpu.pcr_set_tuning(fb, 0, 8, 0, band_filter=band_filter, band_eps=(1, 100), band_bounds=band_bounds)
+    img_h = torch.empty(W * H, dtype=torch.int32, device="cuda")
+    ref = oracle.render_atomicmin(pts, view)
+    sums, ovf = oracle.hq_accumulate(pts, view, ref, 1, 100)
+    assert not ovf
+    for _ in range(2):
+        gpu.pcr_render_hq_splat(fb, dev, view, 1, 100)
+        _, acc = gpu.pcr_framebuffer_keys(fb)
+        got = acc.cpu().numpy().view(np.uint64)
+        assert np.array_equal(got[:, 1] >> 32, sums[3])
+        assert np.array_equal(got[:, 0] & 0xFFFFFFFF, sums[0]) and np.array_equal(got[:, 0] >> 32, sums[1])
+        assert np.array_equal(got[:, 1] & 0xFFFFFFFF, sums[2])
+        gpu.pcr_resolve(fb, img_h, 0, True)
+        assert np.array_equal(img_h.cpu().numpy().view(np.uint32), oracle.resolve_hq(sums))
+        assert gpu.pcr_get_device_status(fb) == gpu.PCR_OK
+    fb.close()
