@@ -141,8 +141,12 @@ def _csrc_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def _traffic(kernel: str, workload: str, n: int):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current kernels."""
+def _traffic(kernel: str, workload: str, n: int, args=None):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current kernels and on this
+    configuration (the exact transform with the default tuning: other transforms and options run other kernels)."""
+    if args is not None and (args.transform != "exact" or getattr(args, "band_filter", False) or
+                             getattr(args, "band_bounds", False)):
+        return None
     path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         with open(path) as f:
@@ -512,7 +516,7 @@ def run_ours(args, wl):
                                 per_kernel["resolve_hq"]) * 1e-3) / 1e9,
         "roofline": {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "peak_kind": peak_kind,
-                     "traffic": _traffic(kernel_name, args.workload, n)},
+                     "traffic": _traffic(kernel_name, args.workload, n, args)},
         "memory_floor": {
             "floor": "max(16 B/point at the measured HBM peak, the pass's framebuffer operations for this cloud "
                      "and view replayed alone in point order without the transform; pass 1: the faster of one "

@@ -32,3 +32,16 @@ def test_digest_covers_the_pass_kernels():
     d = bench._csrc_digest()
     assert len(d) == 16 and int(d, 16) >= 0
     assert d == bench._csrc_digest()
+
+
+def test_traffic_only_for_the_captured_configuration(monkeypatch):
+    """The record was taken on the exact transform with the default tuning: the other transforms and the
+    random-order options run other kernels, so their lines carry no traffic figure."""
+    import argparse
+    e = _record()["k_hq"]["lidar100m"]
+    monkeypatch.setattr(bench, "_csrc_digest", lambda: e["csrc_digest"])
+    base = dict(transform="exact", band_filter=False, band_bounds=False)
+    assert bench._traffic("k_hq", "lidar100m", 100, argparse.Namespace(**base)) == e["bytes_per_point"] * 100
+    for change in (dict(transform="fp64"), dict(transform="double-float"), dict(band_filter=True),
+                   dict(band_bounds=True)):
+        assert bench._traffic("k_hq", "lidar100m", 100, argparse.Namespace(**{**base, **change})) is None
