@@ -147,3 +147,24 @@ def test_band_bounds_and_their_limit(gpu, eps, bounds):
         gpu.pcr_hq_accumulate(fb, _dev(pts), view, *eps)
         _expect(gpu, fb, pts, view, ref, eps)
     fb.close()
+
+
+@pytest.mark.parametrize("n", [0, 1, 31, 63, 64, 65, 129, 4099])
+def test_small_counts_with_both_options(gpu, n):
+    """Band records and band bounds on counts below, at and just past one 64-point tile (the records' unit):
+    keys, sums and counts equal the oracle's, and an empty cloud records nothing and adds nothing."""
+    import torch
+    pts = scenes.cube(n, 300 + n) if n else np.zeros((0, 4), np.uint32)
+    view = scenes.View.lookat((0.2, 0.1, 1.6), (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), 70.0, 33, 17, 0.1, 10.0)
+    fb = gpu.pcr_create_framebuffer(view.width, view.height, gpu.PCR_FB_HQ)
+    gpu.pcr_set_tuning(fb, 0, 8, 0, band_filter=1, band_eps=(1, 100), band_bounds=1)
+    dev = _dev(pts) if n else torch.zeros((0, 4), dtype=torch.int32, device="cuda")
+    for _ in range(2):
+        gpu.pcr_clear(fb)
+        gpu.pcr_render_hq_splat(fb, dev, view, 1, 100)
+        ref = oracle.render_atomicmin(pts, view)
+        keys, _ = gpu.pcr_framebuffer_keys(fb)
+        assert np.array_equal(gpu.keys_to_numpy(keys), ref)
+        _expect(gpu, fb, pts, view, ref)
+    assert gpu.pcr_get_device_status(fb) == gpu.PCR_OK
+    fb.close()
