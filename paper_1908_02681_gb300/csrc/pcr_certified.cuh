@@ -1250,7 +1250,7 @@ __device__ __forceinline__ bool band_accept(const ulonglong2* bounds, const unsi
 // points of a lane are classified before their stored-key reads. The plain exact instance (no band records)
 // is pipelined across tiles: a tile's stored-key reads are tested after the next tile's tier 1, so their L2
 // latency overlaps a whole tile of work. Its carried state needs 85 registers (3 blocks per SM; at 4 it
-// spills); measured on 100M points it is 0.9 % faster in scan order than testing the reads in the same turn at
+// spills); measured on 100M points it is 1.0 % faster in scan order than testing the reads in the same turn at
 // 4 blocks and 64 registers, and 2.7 % faster than that at 3 blocks. The other instances keep 4 blocks.
 #ifndef PCR_HQ_MIN_BLOCKS
 #define PCR_HQ_MIN_BLOCKS 4
