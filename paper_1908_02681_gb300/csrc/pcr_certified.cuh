@@ -1246,17 +1246,11 @@ __device__ __forceinline__ bool band_accept(const ulonglong2* bounds, const unsi
   return in_band(q, stored_key(keys, pix) >> 24, nq, eps_num, eps_den);
 }
 
-// Pass 2 (Section 2.2) with the certified transform, same two tiers and the same point staging as pass 1. Both
-// points of a lane are classified before their stored-key reads. The plain exact instance (no band records)
-// is pipelined across tiles: a tile's stored-key reads are tested after the next tile's tier 1, so their L2
-// latency overlaps a whole tile of work. Its carried state needs 85 registers (3 blocks per SM; at 4 it
-// spills); measured on 100M points it is 1.0 % faster in scan order than testing the reads in the same turn at
-// 4 blocks and 64 registers, and 2.7 % faster than that at 3 blocks. The other instances keep 4 blocks.
+// Pass 2 (Section 2.2) with the certified transform, same two tiers and the same point staging as pass 1, at
+// 64 registers and 4 blocks per SM with both points of a lane classified before their stored-key reads (the
+// fastest measured shape: 1.5 % faster than one point at a time at 48 registers and 5 blocks).
 #ifndef PCR_HQ_MIN_BLOCKS
 #define PCR_HQ_MIN_BLOCKS 4
-#endif
-#ifndef PCR_HQ_PIPE_MIN_BLOCKS
-#define PCR_HQ_PIPE_MIN_BLOCKS 3
 #endif
 // kBand: only the points whose bit is set in band_mask (written by pass 1 for the same points and view, see
 // BandMask) can be accepted; each warp appends them to a shared-memory candidate queue and classifies them 32
@@ -1264,7 +1258,7 @@ __device__ __forceinline__ bool band_accept(const ulonglong2* bounds, const unsi
 // bounds (exact transform): the pixels' accept bounds from k_band_bounds for this eps, or null (in_band on the
 // stored key). Tier 2 and the arbiter always test against the stored key.
 template <bool kApprox, bool kMerge, bool kRing, bool kBand = false>
-__global__ void __launch_bounds__(kCertThreads, !kApprox && !kBand ? PCR_HQ_PIPE_MIN_BLOCKS : PCR_HQ_MIN_BLOCKS) k_hq_cert(
+__global__ void __launch_bounds__(kCertThreads, PCR_HQ_MIN_BLOCKS) k_hq_cert(
     const uint4* __restrict__ pts, uint64_t n, const __grid_constant__ CertParams P,
     const unsigned long long* __restrict__ keys, unsigned long long* __restrict__ accum, uint32_t eps_num,
     uint32_t eps_den, uint32_t* __restrict__ status, const long long* __restrict__ table,
@@ -1317,14 +1311,8 @@ __global__ void __launch_bounds__(kCertThreads, !kApprox && !kBand ? PCR_HQ_PIPE
     commit_add<kMerge>(e && band_accept(bounds, keys, x, qc, P.v.nq, eps_num, eps_den), x, p.w, accum, lane);
     defer_points(d, p, q, qn, lane, [&](const uint4& dd) { hq_deferred(P, sF, dd, keys, accum, eps_num, eps_den); });
   };
-  // The pipeline's carried state (plain exact instance): the previous tile's decided fragments and their
-  // stored keys, in flight since that tile.
-  bool pe0 = false, pe1 = false;
-  uint32_t px0 = 0, px1 = 0, pc0 = 0, pc1 = 0;
-  unsigned long long pq0 = 0, pq1 = 0, pk0 = 0, pk1 = 0;
   // Both points of the lane's tile are classified first, so that their two stored-key reads are in flight
-  // together; the deferrals go to the queue at once, the band tests and additions follow (one tile later in
-  // the plain exact instance).
+  // together; then the band tests, the additions, the deferrals.
   const bool done = stream_tiles<kRing>(pts, n, ring[warp], bars[warp], lane,
                                         [&](const uint4& p0, bool v0, const uint4& p1, bool v1, uint64_t tile) {
     if constexpr (kBand) {
@@ -1356,35 +1344,25 @@ __global__ void __launch_bounds__(kCertThreads, !kApprox && !kBand ? PCR_HQ_PIPE
       unsigned long long q0, q1;
       frag(p0, v0, e0, d0, x0, q0);
       frag(p1, v1, e1, d1, x1, q1);
-      auto tier2 = [&](const uint4& d) { hq_deferred(P, sF, d, keys, accum, eps_num, eps_den); };
-      defer_points(d0, p0, q, qn, lane, tier2);
-      defer_points(d1, p1, q, qn, lane, tier2);
+      bool a0, a1;
       if (bounds) {
         const ulonglong2 b0 = e0 ? __ldcg(bounds + x0) : make_ulonglong2(1ull, 0ull);
         const ulonglong2 b1 = e1 ? __ldcg(bounds + x1) : make_ulonglong2(1ull, 0ull);
-        commit_add<kMerge>(q0 >= b0.x && q0 <= b0.y, x0, p0.w, accum, lane);
-        commit_add<kMerge>(q1 >= b1.x && q1 <= b1.y, x1, p1.w, accum, lane);
+        a0 = q0 >= b0.x && q0 <= b0.y;
+        a1 = q1 >= b1.x && q1 <= b1.y;
       } else {
-        // the previous tile's band tests, then this tile's reads, tested next turn
-        commit_add<kMerge>(pe0 && in_band(pq0, pk0 >> 24, P.v.nq, eps_num, eps_den), px0, pc0, accum, lane);
-        commit_add<kMerge>(pe1 && in_band(pq1, pk1 >> 24, P.v.nq, eps_num, eps_den), px1, pc1, accum, lane);
-        pk0 = e0 ? stored_key(keys, x0) : 0ull;
-        pk1 = e1 ? stored_key(keys, x1) : 0ull;
-        pe0 = e0;
-        pe1 = e1;
-        px0 = x0;
-        px1 = x1;
-        pq0 = q0;
-        pq1 = q1;
-        pc0 = p0.w;
-        pc1 = p1.w;
+        const unsigned long long m0 = e0 ? stored_key(keys, x0) >> 24 : 0ull;
+        const unsigned long long m1 = e1 ? stored_key(keys, x1) >> 24 : 0ull;
+        a0 = e0 && in_band(q0, m0, P.v.nq, eps_num, eps_den);
+        a1 = e1 && in_band(q1, m1, P.v.nq, eps_num, eps_den);
       }
+      commit_add<kMerge>(a0, x0, p0.w, accum, lane);
+      commit_add<kMerge>(a1, x1, p1.w, accum, lane);
+      auto tier2 = [&](const uint4& d) { hq_deferred(P, sF, d, keys, accum, eps_num, eps_den); };
+      defer_points(d0, p0, q, qn, lane, tier2);
+      defer_points(d1, p1, q, qn, lane, tier2);
     }
   });
-  if constexpr (!kApprox && !kBand) {  // the last tile's band tests (nothing pending with bounds or no tiles)
-    commit_add<kMerge>(pe0 && in_band(pq0, pk0 >> 24, P.v.nq, eps_num, eps_den), px0, pc0, accum, lane);
-    commit_add<kMerge>(pe1 && in_band(pq1, pk1 >> 24, P.v.nq, eps_num, eps_den), px1, pc1, accum, lane);
-  }
   if (!done && lane == 0) atomicOr(status, kStatusTimeout);
   if constexpr (kBand) {  // the last candidates (fewer than 32)
     const uint4 c = cq[lane < cn ? lane : 0];
