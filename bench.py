@@ -29,6 +29,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -131,13 +132,21 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def _code_only(text: str) -> str:
+    """C++ source without its comments and with whitespace runs collapsed (the code tokens that a build sees)."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return re.sub(r"\s+", " ", text).strip()
+
+
 def _csrc_digest() -> str:
-    """Digest of the sources that define the two point-pass kernels (k_raster_cert, k_hq_cert)."""
+    """Digest of the code (comments and layout aside) that defines the two point-pass kernels (k_raster_cert,
+    k_hq_cert)."""
     h = hashlib.sha256()
     for name in ("pcr_certified.cuh", "pcr_device.cuh", "pcr_kernels.cuh"):
         f = os.path.join(ROOT, "paper_1908_02681_gb300", "csrc", name)
-        with open(f, "rb") as fh:
-            h.update(os.path.basename(f).encode() + fh.read())
+        with open(f, encoding="utf-8") as fh:
+            h.update(name.encode() + _code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

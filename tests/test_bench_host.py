@@ -45,3 +45,11 @@ def test_traffic_only_for_the_captured_configuration(monkeypatch):
     for change in (dict(transform="fp64"), dict(transform="double-float"), dict(band_filter=True),
                    dict(band_bounds=True)):
         assert bench._traffic("k_hq", "lidar100m", 100, argparse.Namespace(**{**base, **change})) is None
+
+
+def test_digest_ignores_comments_and_layout():
+    code = "int f(int a) {\n  return a + 1;  // one more\n}\n"
+    same = "/* header */ int f(int a) { return a + 1; }"
+    other = "int f(int a) { return a + 2; }"
+    assert bench._code_only(code) == bench._code_only(same)
+    assert bench._code_only(code) != bench._code_only(other)
