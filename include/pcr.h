@@ -97,8 +97,9 @@ typedef struct {
 /* Launch tuning of a framebuffer's point passes (the knobs an autotuner sets). Results never depend on it. */
 typedef struct {
   int32_t merge_same_pixel; /* 1: the fragments of one warp that land on the same pixel are merged with warp
-                               reductions, then one atomic per pixel; 0 (default): one atomic per fragment
-                               (in pass 1 only where the fragment's key is below the key the pixel holds) */
+                               reductions, then one atomic per pixel; 0 (default): pass 1 issues one atomic
+                               per fragment whose key is below the key the pixel holds, and pass 2 merges the
+                               additions of two adjacent lanes (consecutive points) that land on one pixel */
   int32_t blocks_per_sm;    /* 256-thread blocks per SM for the point passes, 1..32 (default 8; capped at the
                                blocks that can be resident, 4 for pass 1 and 5 for pass 2) */
   int32_t staging;          /* how each warp brings its tiles of 64 points in: 0 (default) its own 16-byte

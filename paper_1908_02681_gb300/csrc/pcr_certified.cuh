@@ -1177,6 +1177,29 @@ __device__ __forceinline__ void commit_add(bool add, uint32_t pix, uint32_t rgba
   }
 }
 
+// Adds the colours of the accepted fragments, merged in lane pairs: lanes 2k and 2k + 1 hold consecutive points
+// (a warp's tiles and candidate batches are in point order), so on a scan-ordered cloud they often add to one
+// pixel; lane 2k then adds both colours with one pair of atomics and lane 2k + 1 none (per-channel sums of two
+// fragments: no carry between the packed fields). Three shuffles per point. Measured in the 100M-point frame
+// on one GPU: pass 2 3.5 % faster in scan order and 3.9 % shuffled than one pair of atomics per fragment;
+// merging groups of 4 or 8 lanes the same way (64-bit sums shuffled) was slower. All lanes must call it.
+__device__ __forceinline__ void commit_add_pairs(bool add, uint32_t pix, uint32_t rgba, unsigned long long* accum,
+                                                 uint32_t lane) {
+  const uint32_t key = add ? pix : 0xFFFFFFFFu;  // pixel indices stay below 2^28
+  const uint32_t key_next = __shfl_down_sync(0xFFFFFFFFu, key, 1);
+  const uint32_t key_prev = __shfl_up_sync(0xFFFFFFFFu, key, 1);
+  const uint32_t rgba_next = __shfl_down_sync(0xFFFFFFFFu, rgba, 1);
+  const bool even = (lane & 1u) == 0u;
+  if (!add || (!even && key_prev == key)) return;  // nothing to add, or added by lane 2k
+  unsigned long long rg = hq_rg(rgba), bc = hq_bc(rgba);
+  if (even && key_next == key) {
+    rg += hq_rg(rgba_next);
+    bc += hq_bc(rgba_next);
+  }
+  atomicAdd(accum + 2 * (uint64_t)pix, rg);
+  atomicAdd(accum + 2 * (uint64_t)pix + 1, bc);
+}
+
 __device__ __noinline__ void hq_deferred(const CertParams& P, const long long* sF, uint4 p,
                                          const unsigned long long* keys, unsigned long long* accum, uint32_t eps_num,
                                          uint32_t eps_den) {
@@ -1274,6 +1297,13 @@ __global__ void __launch_bounds__(kCertThreads, PCR_HQ_MIN_BLOCKS) k_hq_cert(
   if (!kApprox) load_table(P, table, sF);
   uint4* q = queue[warp];
   uint32_t qn = 0;
+  // The additions of accepted fragments: warp-level same-pixel merging (kMerge), else lane pairs.
+  auto add = [&](bool accept, uint32_t pix, uint32_t rgba) {
+    if constexpr (kMerge)
+      commit_add<true>(accept, pix, rgba, accum, lane);
+    else
+      commit_add_pairs(accept, pix, rgba, accum, lane);
+  };
   // Double-float mode, per point: the evaluation, the band test against the stored key, the additions.
   auto point_df = [&](const uint4& p, bool valid) {
     bool accept = false;
@@ -1283,7 +1313,7 @@ __global__ void __launch_bounds__(kCertThreads, PCR_HQ_MIN_BLOCKS) k_hq_cert(
       pix = f.pixel;
       hq_decide(P, f, keys, eps_num, eps_den, &accept);
     }
-    commit_add<kMerge>(accept, pix, p.w, accum, lane);
+    add(accept, pix, p.w);
   };
   // Exact mode, tier 1 of one point: decided (exact code), or deferred to tier 2 (undecided pixel, or a code
   // undecided between two neighbours: rare, and settling it here would cost every point a second band test).
@@ -1308,7 +1338,7 @@ __global__ void __launch_bounds__(kCertThreads, PCR_HQ_MIN_BLOCKS) k_hq_cert(
     uint32_t x;
     unsigned long long qc;
     frag(p, valid, e, d, x, qc);
-    commit_add<kMerge>(e && band_accept(bounds, keys, x, qc, P.v.nq, eps_num, eps_den), x, p.w, accum, lane);
+    add(e && band_accept(bounds, keys, x, qc, P.v.nq, eps_num, eps_den), x, p.w);
     defer_points(d, p, q, qn, lane, [&](const uint4& dd) { hq_deferred(P, sF, dd, keys, accum, eps_num, eps_den); });
   };
   // Both points of the lane's tile are classified first, so that their two stored-key reads are in flight
@@ -1356,8 +1386,8 @@ __global__ void __launch_bounds__(kCertThreads, PCR_HQ_MIN_BLOCKS) k_hq_cert(
         a0 = e0 && in_band(q0, m0, P.v.nq, eps_num, eps_den);
         a1 = e1 && in_band(q1, m1, P.v.nq, eps_num, eps_den);
       }
-      commit_add<kMerge>(a0, x0, p0.w, accum, lane);
-      commit_add<kMerge>(a1, x1, p1.w, accum, lane);
+      add(a0, x0, p0.w);
+      add(a1, x1, p1.w);
       auto tier2 = [&](const uint4& d) { hq_deferred(P, sF, d, keys, accum, eps_num, eps_den); };
       defer_points(d0, p0, q, qn, lane, tier2);
       defer_points(d1, p1, q, qn, lane, tier2);
