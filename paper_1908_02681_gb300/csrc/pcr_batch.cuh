@@ -251,7 +251,10 @@ __global__ void __launch_bounds__(kCertThreads, PCR_BATCH_MIN_BLOCKS) k_batch_pa
           if (f.state == kExact)
             accept = in_band(code_from_fixed(f.a1, f.a2), stored_key(keys, pix) >> 24, Pg.v.nq, eps_num, eps_den);
         }
-        commit_add<kMerge>(accept, pix, p.w, accum, lane, seg);
+        if constexpr (kMerge)
+          commit_add<true>(accept, pix, p.w, accum, lane, seg);
+        else  // consecutive points in adjacent lanes: merged in lane pairs (commit_add_pairs)
+          commit_add_pairs(accept, pix, p.w, accum, lane);
         defer_points(defer, p, q, qn, lane,
                      [&](const uint4& d) { hq_deferred(Pg, sF, d, keys, accum, eps_num, eps_den); });
       }
