@@ -239,7 +239,8 @@ pcr_status launch_raster(pcr_framebuffer* fb, const pcr_point* d_points, uint64_
     return after_launch("k_raster_fp64");
   }
   const long long* table = fb_table(fb, dv, transform, s);
-  const pcr::BandMask bm{band.on ? fb->band_mask + 2 * band.tile_offset : nullptr, band.num, band.den};
+  const pcr::BandMask bm = pcr::band_mask(band.on ? fb->band_mask + 2 * band.tile_offset : nullptr, band.num,
+                                          band.den, dv.nq);
   return pcr::launch_raster_certified(pts, n, dv, transform == PCR_TRANSFORM_DOUBLE_FLOAT, fb->keys, fb->status,
                                       sm_count(fb->device), s, stats, fb->tuning, table, bm)
              ? after_launch("k_raster_certified")

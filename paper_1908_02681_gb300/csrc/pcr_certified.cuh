@@ -1040,18 +1040,40 @@ __device__ __forceinline__ void defer_points(bool defer, const uint4& p, uint4* 
 // the ranges' tables in dynamic shared memory (P.n_pw blocks of 3 * kTableEntries entries, from the device table).
 // kBand: also writes the band mask for pass 2 (band.mask: two words per tile of 64 points, bit lane of word
 // 2 tile + k for point 64 tile + 32 k + lane): the bit is clear when the point is culled, or when its key is
-// certainly outside the final band of eps = band.num / band.den: eps_den (q - qs) > eps_num (qs + Nq) with qs
-// the code its pixel held when it was read, which is at least the final minimum (a stored key only decreases).
+// certainly outside the final band of eps = eps_num / eps_den = E + f (E integer, 0 <= f < 1). The test takes
+// the keys' high words only, kh = key >> 32 and sh = sk >> 32 (sk the key its pixel held when it was read), in
+// integers: kh >= sh (1 + E) + floor(sh mf / 2^32) + C + 1, with mf >= f 2^32 and C 2^8 >= 255 (1 + eps) +
+// eps Nq + 1. Since q = key >> 24 >= kh 2^8 and qs = sk >> 24 <= sh 2^8 + 255, that gives q > qs (1 + eps) +
+// eps Nq, i.e. eps_den (q - qs) > eps_num (qs + Nq). The pixel's final minimum is at most qs (a stored key only
+// decreases), so q is beyond the final band too. A point the test cannot place keeps its bit (pass 2 decides).
 struct BandMask {
   uint32_t* mask;
-  uint32_t num, den;
+  uint32_t e1p, mf;      // 1 + E; ceil(f 2^32)
+  unsigned long long c1; // C + 1
 };
+
+inline BandMask band_mask(uint32_t* mask, uint32_t eps_num, uint32_t eps_den, unsigned long long nq) {
+  BandMask b{mask, 1u + eps_num / eps_den, 0u, 0ull};
+  const unsigned __int128 fr = (((unsigned __int128)(eps_num % eps_den)) << 32) + eps_den - 1;  // ceil
+  const unsigned long long mf = (unsigned long long)(fr / eps_den);
+  if (mf >> 32) {  // f 2^32 rounded up to 2^32: one more in the integer part
+    b.e1p += 1u;
+  } else {
+    b.mf = (uint32_t)mf;
+  }
+  // C = ceil((255 (den + num) + num Nq + den) / (256 den))
+  const unsigned __int128 numer = (unsigned __int128)255 * ((unsigned __int128)eps_den + eps_num) +
+                                  (unsigned __int128)eps_num * nq + eps_den;
+  const unsigned __int128 den = (unsigned __int128)256 * eps_den;
+  b.c1 = (unsigned long long)((numer + den - 1) / den) + 1ull;
+  return b;
+}
 
 template <bool kApprox, bool kMerge, bool kStats, bool kRing, int kPw, bool kBand = false>
 __global__ void __launch_bounds__(kCertThreads, kApprox ? PCR_CERT_APPROX_MIN_BLOCKS : PCR_CERT_MIN_BLOCKS) k_raster_cert(
     const uint4* __restrict__ pts, uint64_t n, const __grid_constant__ CertParams P,
     unsigned long long* __restrict__ keys, unsigned long long* __restrict__ stats, uint32_t* __restrict__ status,
-    const long long* __restrict__ table, BandMask band = BandMask{nullptr, 0u, 1u}) {
+    const long long* __restrict__ table, BandMask band = BandMask{nullptr, 1u, 0u, 0ull}) {
   __shared__ long long sF_static[kPw ? 1 : 3 * kTableEntries];
   extern __shared__ __align__(16) long long sF_dynamic[];
   __shared__ uint4 queue[kCertWarps][kQueue];
@@ -1103,9 +1125,9 @@ __global__ void __launch_bounds__(kCertThreads, kApprox ? PCR_CERT_APPROX_MIN_BL
     commit_min<kMerge>(has && key < sk, pix, key, keys, lane);
     bool need = defer;
     if constexpr (kBand) {
-      const unsigned long long qk = key >> 24, qs = sk >> 24;
-      const bool out = qk > qs && (unsigned long long)band.den * (qk - qs) > (unsigned long long)band.num * (qs + P.v.nq);
-      need |= has && !out;
+      const uint32_t kh = (uint32_t)(key >> 32), sh = (uint32_t)(sk >> 32);
+      const unsigned long long bound = (unsigned long long)sh * band.e1p + band.c1 + __umulhi(sh, band.mf);
+      need |= has && !(kh >= bound);
     }
     if (!kApprox)
       defer_points(defer, p, q, qn, lane, [&](const uint4& d) { raster_deferred(P, sF, d, keys, &c_fp64); });
@@ -1441,7 +1463,7 @@ inline unsigned persistent_grid(int resident, uint64_t n, int sms, int per_sm) {
 template <bool kApprox, bool kMerge, bool kStats, bool kRing, int kPw, bool kBand = false>
 inline void raster_launch5(const uint4* pts, uint64_t n, const CertParams& P, unsigned long long* keys,
                            unsigned long long* stats, uint32_t* status, int sms, int per_sm, cudaStream_t s,
-                           const long long* table, BandMask band = BandMask{nullptr, 0u, 1u}) {
+                           const long long* table, BandMask band = BandMask{nullptr, 1u, 0u, 0ull}) {
   auto kernel = k_raster_cert<kApprox, kMerge, kStats, kRing, kPw, kBand>;
   if constexpr (kPw) {
     // the ranges' tables in dynamic shared memory: up to kMaxRanges * 12 KB (opt in above 48 KB once)
@@ -1467,7 +1489,7 @@ inline void raster_launch5(const uint4* pts, uint64_t n, const CertParams& P, un
 template <bool kApprox, bool kMerge, bool kStats, bool kRing>
 inline void raster_launch4(const uint4* pts, uint64_t n, const CertParams& P, unsigned long long* keys,
                            unsigned long long* stats, uint32_t* status, int sms, int per_sm, cudaStream_t s,
-                           const long long* table, BandMask band = BandMask{nullptr, 0u, 1u}) {
+                           const long long* table, BandMask band = BandMask{nullptr, 1u, 0u, 0ull}) {
   if constexpr (!kApprox && !kStats) {
     if (band.mask && P.n_pw == 0) {  // also write the band mask for pass 2
       raster_launch5<false, kMerge, false, kRing, 0, true>(pts, n, P, keys, nullptr, status, sms, per_sm, s, table,
@@ -1488,7 +1510,7 @@ template <bool kApprox, bool kMerge>
 inline void raster_launch(const uint4* pts, uint64_t n, const CertParams& P, unsigned long long* keys,
                           unsigned long long* stats, uint32_t* status, int sms, int per_sm, cudaStream_t s,
                           const long long* table = nullptr, int staging = 0,
-                          BandMask band = BandMask{nullptr, 0u, 1u}) {
+                          BandMask band = BandMask{nullptr, 1u, 0u, 0ull}) {
   if (stats && !kApprox && !kMerge)
     staging ? raster_launch4<false, false, true, true>(pts, n, P, keys, stats, status, sms, per_sm, s, table)
             : raster_launch4<false, false, true, false>(pts, n, P, keys, stats, status, sms, per_sm, s, table);
@@ -1530,7 +1552,7 @@ inline int table_blocks(const CertParams& P) { return P.n_pw > 0 ? P.n_pw : 1; }
 inline bool launch_raster_certified(const uint4* pts, uint64_t n, const DevView& v, bool approximate,
                                     unsigned long long* keys, uint32_t* status, int sms, cudaStream_t s,
                                     unsigned long long* stats = nullptr, const Tuning& t = Tuning(),
-                                    const long long* table = nullptr, BandMask band = BandMask{nullptr, 0u, 1u}) {
+                                    const long long* table = nullptr, BandMask band = BandMask{nullptr, 1u, 0u, 0ull}) {
   const CertParams* Pp = nullptr;
   const unsigned grid = cert_grid(n, sms, t.blocks_per_sm);
   // PIECEWISE views need the device copy of their tables

@@ -115,3 +115,47 @@ def test_invariant_divisor_division_is_exact():
         for n in ns:
             n &= M64
             assert div_by(n, mg) == n // d, (n, d)
+
+
+def band_record_constants(num, den, nq):
+    """band_mask restated: 1 + E, mf = ceil(f 2^32) (with the carry into E), C + 1."""
+    e1p = 1 + num // den
+    mf = -(-((num % den) << 32) // den)
+    if mf >> 32:
+        e1p, mf = e1p + 1, 0
+    c = -(-(255 * (den + num) + num * nq + den) // (256 * den))
+    return e1p, mf, c + 1
+
+
+def band_record_out(key, sk, consts):
+    """Pass 1's band-record test on the keys' high words: the point is dropped when this is true."""
+    e1p, mf, c1 = consts
+    kh, sh = key >> 32, sk >> 32
+    return kh >= sh * e1p + c1 + ((sh * mf) >> 32)
+
+
+def test_band_record_test_is_conservative():
+    """Pass 1's band record drops a point only when kh >= sh (1 + E) + floor(sh mf / 2^32) + C + 1 on the keys'
+    high words: this must imply the exact u64 condition q > qs and eps_den (q - qs) > eps_num (qs + Nq) for
+    q = key >> 24, qs = sk >> 24, at keys placed just below, on and above the band's edge, for empty pixels and
+    several eps and Nq; and it must still drop points well beyond the band."""
+    rng = random.Random(10)
+    n_out = 0
+    for nq in (0, 1 << 20, 109951162777, (1 << 40) - 1):
+        for num, den in ((1, 100), (3, 7), (1, 1 << 20), (5, 3), (100, 1), ((1 << 20) - 1, 1 << 20)):
+            consts = band_record_constants(num, den, nq)
+            for _ in range(300):
+                qs = rng.choice([rng.randrange(1 << 40), rng.randrange(1 << 30), (1 << 40) - 1, 1])
+                sk = (qs << 24) | rng.randrange(1 << 24)
+                if rng.random() < 0.05:
+                    sk = M64  # empty pixel
+                edge = qs + (num * (qs + nq)) // den  # the last code in the band
+                for dq in (-2, -1, 0, 1, 2, 3, 1 << 8, 1 << 10, 1 << 20, rng.randrange(1 << 30)):
+                    q = min(max(edge + dq, 0), (1 << 40) - 2)
+                    key = (q << 24) | rng.randrange(1 << 24)
+                    if not band_record_out(key, sk, consts):
+                        continue
+                    n_out += 1
+                    qq, qqs = key >> 24, sk >> 24
+                    assert qq > qqs and den * (qq - qqs) > num * (qqs + nq), (key, sk, num, den, nq)
+    assert n_out > 1000  # the test does drop points
