@@ -114,8 +114,8 @@ typedef struct {
                                whose code is already beyond the band of the key its pixel held can never be
                                accepted. pcr_render_hq_splat and pcr_render_frame_host do the same between
                                their two passes. 0 (default): nothing is recorded. It pays off when points come
-                               in random order (pass 2 about 20 % faster), not in scan order, where pass 1's
-                               extra work outweighs it; the autotuner tries both. The first
+                               in random order (pass 2 about 17 % faster, the HQ frame about 5 %), not in scan
+                               order, where pass 1's extra work outweighs it; the autotuner tries both. The first
                                recording of n points allocates n / 8 bytes of device memory (not during stream
                                capture, where nothing is recorded); a clear drops the record. */
   uint32_t band_eps_num, band_eps_den; /* eps of the records (default 1 / 100); band_eps_den in 1..2^20 */
@@ -124,8 +124,8 @@ typedef struct {
                                24 B per pixel) and tests each decided code q by lo <= q <= hi, where the host
                                finds eps_num * (2^40 + Nq) + eps_den * 2^40 <= 2^64 (the same decision as the
                                band test of pcr_render_hq_splat then); 0 (default): the band test on the stored
-                               key. Faster for points in random order (pass 2 about 5 %), slower by the extra
-                               kernel in scan order; the autotuner tries both. */
+                               key. Faster for points in random order without band records (pass 2 about 6 %),
+                               slower by the extra kernel in scan order; the autotuner tries both. */
 } pcr_tuning;
 
 /* Framebuffer flags. */
