@@ -1065,7 +1065,16 @@ inline BandMask band_mask(uint32_t* mask, uint32_t eps_num, uint32_t eps_den, un
   const unsigned __int128 numer = (unsigned __int128)255 * ((unsigned __int128)eps_den + eps_num) +
                                   (unsigned __int128)eps_num * nq + eps_den;
   const unsigned __int128 den = (unsigned __int128)256 * eps_den;
-  b.c1 = (unsigned long long)((numer + den - 1) / den) + 1ull;
+  const unsigned __int128 c = (numer + den - 1) / den;
+  if (b.e1p > (1u << 24) || c > ((unsigned __int128)1 << 56)) {
+    // an eps this large leaves no code beyond the band worth dropping: the record keeps every point (a bound of
+    // 2^62 exceeds every high word, and the sum cannot wrap)
+    b.e1p = 0u;
+    b.mf = 0u;
+    b.c1 = 1ull << 62;
+  } else {
+    b.c1 = (unsigned long long)c + 1ull;  // sh e1p + c1 + umulhi < 2^56 + 2^56 + 2^32: no wrap
+  }
   return b;
 }
 

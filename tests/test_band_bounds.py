@@ -124,6 +124,8 @@ def band_record_constants(num, den, nq):
     if mf >> 32:
         e1p, mf = e1p + 1, 0
     c = -(-(255 * (den + num) + num * nq + den) // (256 * den))
+    if e1p > 1 << 24 or c > 1 << 56:
+        return 0, 0, 1 << 62
     return e1p, mf, c + 1
 
 
@@ -159,3 +161,15 @@ def test_band_record_test_is_conservative():
                     qq, qqs = key >> 24, sk >> 24
                     assert qq > qqs and den * (qq - qqs) > num * (qqs + nq), (key, sk, num, den, nq)
     assert n_out > 1000  # the test does drop points
+
+
+def test_band_record_constants_never_wrap():
+    """At the largest eps and Nq the API admits, the record's 64-bit bound sh (1 + E) + C + 1 + floor(sh mf /
+    2^32) stays below 2^64, and where it would not, the record keeps every point."""
+    for nq in (0, (1 << 40) - 1):
+        for num, den in (((1 << 32) - 1, 1), ((1 << 24) - 1, 1), (1, 1), ((1 << 20) - 1, 1 << 20), (1 << 31, 3)):
+            e1p, mf, c1 = band_record_constants(num, den, nq)
+            sh = (1 << 32) - 1
+            assert sh * e1p + c1 + ((sh * mf) >> 32) < 1 << 63
+            if (e1p, mf, c1) == (0, 0, 1 << 62):
+                assert not band_record_out(M64 - 1, 0, (e1p, mf, c1))  # nothing is dropped

@@ -168,3 +168,26 @@ def test_small_counts_with_both_options(gpu, n):
         _expect(gpu, fb, pts, view, ref)
     assert gpu.pcr_get_device_status(fb) == gpu.PCR_OK
     fb.close()
+
+
+@pytest.mark.parametrize("metric", [False, True])
+@pytest.mark.parametrize("eps", [(1, 100), (3, 7), (1, 1 << 20), (5, 3), (1 << 23, 3)])
+def test_band_records_across_eps(gpu, eps, metric):
+    """Band records written and used at several eps (the record's high-word test with its integer and fraction
+    parts of eps, and its constant C from Nq), on a LINEAR (Nq > 0) and a METRIC (Nq = 0) view, shuffled so that
+    the records drop many points: sums and counts equal the oracle's."""
+    from tests.helpers import RawView
+    pts = scenes.lidar(1_500_007, 87)
+    scenes.shuffle(pts, 9)
+    base = scenes.lidar_1km_view(640, 360)
+    view = RawView(base.view_proj, base.near, base.far, 640, 360, depth_mode=1 if metric else 0,
+                   metric_scale=1000.0)
+    dev = _dev(pts)
+    fb = gpu.pcr_create_framebuffer(view.width, view.height, gpu.PCR_FB_HQ)
+    gpu.pcr_set_tuning(fb, 0, 8, 0, band_filter=1, band_eps=eps)
+    gpu.pcr_render_hq_splat(fb, dev, view, *eps)
+    ref = oracle.render_atomicmin(pts, view)
+    keys, _ = gpu.pcr_framebuffer_keys(fb)
+    assert np.array_equal(gpu.keys_to_numpy(keys), ref)
+    _expect(gpu, fb, pts, view, ref, eps)
+    fb.close()
