@@ -224,7 +224,7 @@ def _config(wl, args, n, world=1):
     view = wl["view"]
     return {"workload": wl["desc"], "points": n, "width": view.width, "height": view.height,
             "transform": args.transform,
-            "step": "atomicMin pass + basic resolve + HQ band pass + HQ resolve with clear",
+            "step": "atomicMin pass + HQ band pass + one resolve of both images (basic and HQ) with clear",
             "band_filter": "on: pass 1 records the points that may be in the eps band, pass 2 skips the others "
                            "(exact)" if getattr(args, "band_filter", False) else "off",
             "band_bounds": "on: pass 2 tests codes against per-pixel bounds from one extra kernel (exact)"
@@ -357,7 +357,7 @@ def run_ours(args, wl):
     pcr.pcr_set_tuning(fb, 0, 8, 0, band_filter=1 if args.band_filter else 0, band_eps=eps,
                        band_bounds=1 if args.band_bounds else 0)
 
-    names = ["raster_atomicmin", "resolve_basic", "hq_accumulate", "resolve_hq"]
+    names = ["raster_atomicmin", "hq_accumulate", "resolve"]
 
     def frame(evs=None):
         def mark(i):
@@ -366,12 +366,11 @@ def run_ours(args, wl):
         mark(0)
         pcr.pcr_render_atomicmin(fb, pts, view, stream)
         mark(1)
-        pcr.pcr_resolve_basic(fb, img_basic, 0, False, stream)
-        mark(2)
         pcr.pcr_hq_accumulate(fb, pts, view, *eps, stream)
+        mark(2)
+        # both images (the basic one from the keys, the HQ one from the sums) and the clear, in one pass
+        pcr.pcr_resolve_both(fb, img_basic, img_hq, 0, True, stream)
         mark(3)
-        pcr.pcr_resolve(fb, img_hq, 0, True, stream)
-        mark(4)
 
     # roofline probes: measured random u64 atomic rate at this framebuffer size, streaming read rate
     ceil = ctypes.CDLL(pcr_build.build_ceilings())
@@ -420,7 +419,7 @@ def run_ours(args, wl):
     for _ in range(args.warmup):
         frame()
     torch.cuda.synchronize()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)] for _ in range(args.steps)]
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if dist:
         dist.barrier()
@@ -522,7 +521,7 @@ def run_ours(args, wl):
         "kernels_ms": per_kernel,
         "atomicmin_gpts": pass1_pts / 1e9,
         "hq_splat_gpts": n / ((per_kernel["raster_atomicmin"] + per_kernel["hq_accumulate"] +
-                                per_kernel["resolve_hq"]) * 1e-3) / 1e9,
+                                per_kernel["resolve"]) * 1e-3) / 1e9,
         "roofline": {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "peak_kind": peak_kind,
                      "traffic": _traffic(kernel_name, args.workload, n, args)},

@@ -223,6 +223,13 @@ pcr_status pcr_resolve(pcr_framebuffer* fb, uint32_t* d_rgba_out, uint32_t backg
 pcr_status pcr_resolve_basic(pcr_framebuffer* fb, uint32_t* d_rgba_out, uint32_t background_rgba,
                              int32_t clear_after, pcr_stream_t stream);
 
+/* Sections 2.1 and 2.2 resolves of an HQ framebuffer in one pass over its pixels: d_rgba_basic gets the
+ * image of pcr_resolve_basic and d_rgba_hq the image of pcr_resolve (the same values, the overflow status
+ * as pcr_resolve sets it); both W*H, caller-owned device memory. clear_after != 0 clears the keys and the sums.
+ * PCR_ERR_INVALID_ARG without PCR_FB_HQ or with a NULL image. */
+pcr_status pcr_resolve_both(pcr_framebuffer* fb, uint32_t* d_rgba_basic, uint32_t* d_rgba_hq, uint32_t background_rgba,
+                            int32_t clear_after, pcr_stream_t stream);
+
 /* Read-only device pointers to the key buffer (width * height u64) and, for HQ framebuffers, the sums
  * (width * height pairs of u64: {R | G << 32, B | count << 32}); *d_accum = NULL otherwise. Valid until
  * pcr_destroy_framebuffer. Either output pointer may be NULL. */

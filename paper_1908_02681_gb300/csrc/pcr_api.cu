@@ -608,6 +608,18 @@ pcr_status pcr_resolve_basic(pcr_framebuffer* fb, uint32_t* d_rgba_out, uint32_t
   return after_launch("k_resolve_basic");
 }
 
+pcr_status pcr_resolve_both(pcr_framebuffer* fb, uint32_t* d_rgba_basic, uint32_t* d_rgba_hq, uint32_t background_rgba,
+                            int32_t clear_after, pcr_stream_t stream) {
+  if (pcr_status st = check_fb(fb)) return st;
+  if (!(fb->flags & PCR_FB_HQ)) return fail(PCR_ERR_INVALID_ARG, "framebuffer was created without PCR_FB_HQ");
+  if (!d_rgba_basic || !d_rgba_hq) return fail(PCR_ERR_INVALID_ARG, "an output image is NULL");
+  const uint64_t npx = (uint64_t)fb->width * fb->height;
+  if (clear_after) fb->band_valid = false;
+  pcr::k_resolve_both<<<grid_for(npx, 256, fb->device, 4), 256, 0, (cudaStream_t)stream>>>(
+      fb->keys, fb->accum, d_rgba_basic, d_rgba_hq, npx, background_rgba, clear_after != 0, fb->status);
+  return after_launch("k_resolve_both");
+}
+
 pcr_status pcr_framebuffer_keys(const pcr_framebuffer* fb, const uint64_t** d_keys, const uint64_t** d_accum) {
   if (pcr_status st = check_fb(fb)) return st;
   if (d_keys) *d_keys = reinterpret_cast<const uint64_t*>(fb->keys);
@@ -693,9 +705,9 @@ pcr_status pcr_render_frame_host(pcr_framebuffer* fb, const pcr_point* h_points,
   if (hq && n > 0)
     if (pcr_status st = launch_hq(fb, d_points, n, dv, view->transform, eps_num, eps_den, s)) return st;
   const uint64_t npx = (uint64_t)fb->width * fb->height;
-  if (pcr_status st = pcr_resolve_basic(fb, d_images, background_rgba, hq ? 0 : 1, stream)) return st;
-  if (hq)
-    if (pcr_status st = pcr_resolve(fb, d_images + npx, background_rgba, 1, stream)) return st;
+  if (pcr_status st = hq ? pcr_resolve_both(fb, d_images, d_images + npx, background_rgba, 1, stream)
+                         : pcr_resolve_basic(fb, d_images, background_rgba, 1, stream))
+    return st;
   e = cudaMemcpyAsync(h_basic, d_images, npx * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && hq) e = cudaMemcpyAsync(h_hq, d_images + npx, npx * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return cuda_fail(e, "image download");

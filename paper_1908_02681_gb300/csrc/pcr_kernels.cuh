@@ -84,8 +84,15 @@ __global__ void k_resolve_hq(ulonglong2* __restrict__ accum, unsigned long long*
     const uint32_t c = (uint32_t)(a.y >> 32);
     if (c == 0) {
       rgba[i] = background;
-    } else {
-      overflow |= c > (1u << 24);
+    } else if (c <= (1u << 24)) {
+      // each channel sum is at most 255 c, so sum + c / 2 < 2^32: the 32-bit quotient is the same
+      const uint32_t h = c / 2;
+      const uint32_t r = ((uint32_t)a.x + h) / c;
+      const uint32_t g = ((uint32_t)(a.x >> 32) + h) / c;
+      const uint32_t b = ((uint32_t)a.y + h) / c;
+      rgba[i] = (r & 0xFFu) | ((g & 0xFFu) << 8) | ((b & 0xFFu) << 16) | 0xFF000000u;
+    } else {  // more fragments than the sums can hold: flagged; the same arithmetic as the oracle's, in 64 bits
+      overflow = true;
       const uint32_t r = (uint32_t)(((a.x & 0xFFFFFFFFull) + c / 2) / c);
       const uint32_t g = (uint32_t)(((a.x >> 32) + c / 2) / c);
       const uint32_t b = (uint32_t)(((a.y & 0xFFFFFFFFull) + c / 2) / c);
@@ -94,6 +101,44 @@ __global__ void k_resolve_hq(ulonglong2* __restrict__ accum, unsigned long long*
     if (clear) {
       accum[i] = make_ulonglong2(0ull, 0ull);
       keys[i] = kEmptyKey;
+    }
+  }
+  if (overflow) atomicOr(status, kStatusOverflow);
+}
+
+// Both resolves of an HQ frame in one pass over the pixels (Section 2.1 from the keys, Section 2.2 from the
+// sums): each pixel's key and sums are read once and both images written, the same values as k_resolve_basic
+// and k_resolve_hq; optional clear of both buffers.
+__global__ void k_resolve_both(unsigned long long* __restrict__ keys, ulonglong2* __restrict__ accum,
+                               uint32_t* __restrict__ rgba_basic, uint32_t* __restrict__ rgba_hq, uint64_t npx,
+                               uint32_t background, int clear, uint32_t* __restrict__ status) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  bool overflow = false;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npx; i += stride) {
+    const unsigned long long k = keys[i];
+    const ulonglong2 a = accum[i];
+    rgba_basic[i] = k == kEmptyKey ? background : ((uint32_t)(k & 0xFFFFFFu) | 0xFF000000u);
+    const uint32_t c = (uint32_t)(a.y >> 32);
+    uint32_t r, g, b;
+    if (c == 0) {
+      rgba_hq[i] = background;
+    } else {
+      if (c <= (1u << 24)) {  // as in k_resolve_hq: 32-bit quotients below the overflow bound
+        const uint32_t h = c / 2;
+        r = ((uint32_t)a.x + h) / c;
+        g = ((uint32_t)(a.x >> 32) + h) / c;
+        b = ((uint32_t)a.y + h) / c;
+      } else {
+        overflow = true;
+        r = (uint32_t)(((a.x & 0xFFFFFFFFull) + c / 2) / c);
+        g = (uint32_t)(((a.x >> 32) + c / 2) / c);
+        b = (uint32_t)(((a.y & 0xFFFFFFFFull) + c / 2) / c);
+      }
+      rgba_hq[i] = (r & 0xFFu) | ((g & 0xFFu) << 8) | ((b & 0xFFu) << 16) | 0xFF000000u;
+    }
+    if (clear) {
+      keys[i] = kEmptyKey;
+      accum[i] = make_ulonglong2(0ull, 0ull);
     }
   }
   if (overflow) atomicOr(status, kStatusOverflow);

@@ -89,6 +89,7 @@ def _declare(lib):
                                _P], S),
         "pcr_resolve": ([_P, _P, ctypes.c_uint32, ctypes.c_int32, _P], S),
         "pcr_resolve_basic": ([_P, _P, ctypes.c_uint32, ctypes.c_int32, _P], S),
+        "pcr_resolve_both": ([_P, _P, _P, ctypes.c_uint32, ctypes.c_int32, _P], S),
         "pcr_framebuffer_keys": ([_P, ctypes.POINTER(_P), ctypes.POINTER(_P)], S),
         "pcr_get_device_status": ([_P, _P], S),
         "pcr_check_bounded_wait": ([_P, ctypes.c_uint32, _P], S),
@@ -331,6 +332,13 @@ def pcr_resolve_basic(fb: Framebuffer, out, background_rgba: int = 0, clear_afte
     _check(load().pcr_resolve_basic(fb.handle, _image_ptr(fb, out), background_rgba & 0xFFFFFFFF, int(clear_after),
                                     _stream(stream)))
     return out
+
+
+def pcr_resolve_both(fb: Framebuffer, out_basic, out_hq, background_rgba: int = 0, clear_after: bool = True,
+                     stream=None):
+    _check(load().pcr_resolve_both(fb.handle, _image_ptr(fb, out_basic), _image_ptr(fb, out_hq),
+                                   background_rgba & 0xFFFFFFFF, int(clear_after), _stream(stream)))
+    return out_basic, out_hq
 
 
 def pcr_framebuffer_keys(fb: Framebuffer):

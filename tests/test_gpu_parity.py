@@ -304,3 +304,30 @@ def test_tuning_does_not_change_results(gpu, merge, blocks, staging):
         gpu.pcr_set_tuning(fb, 1, 0)
     with pytest.raises(gpu.PcrError):
         gpu.pcr_set_tuning(fb, 0, 8, 2)
+
+
+def test_resolve_both_equals_the_two_resolves(gpu):
+    """pcr_resolve_both writes the basic and the HQ image in one pass: both equal the oracle's resolves (with a
+    background), and the framebuffer is left cleared."""
+    import torch
+    pts = scenes.lidar(2_000_003, 31)
+    view = scenes.lidar_1km_view(800, 450)
+    fb = gpu.pcr_create_framebuffer(view.width, view.height, gpu.PCR_FB_HQ)
+    gpu.pcr_render_hq_splat(fb, _dev(pts), view, 1, 100)
+    ref = oracle.render_atomicmin(pts, view)
+    sums, ovf = oracle.hq_accumulate(pts, view, ref, 1, 100)
+    assert not ovf
+    npx = view.width * view.height
+    img_b = torch.empty(npx, dtype=torch.int32, device="cuda")
+    img_h = torch.empty(npx, dtype=torch.int32, device="cuda")
+    gpu.pcr_resolve_both(fb, img_b, img_h, 0x01020304, True)
+    assert np.array_equal(img_b.cpu().numpy().view(np.uint32), oracle.resolve_basic(ref, 0x01020304))
+    assert np.array_equal(img_h.cpu().numpy().view(np.uint32), oracle.resolve_hq(sums, 0x01020304))
+    keys, acc = gpu.pcr_framebuffer_keys(fb)
+    assert bool((keys == -1).all()) and bool((acc == 0).all())
+    assert gpu.pcr_get_device_status(fb) == gpu.PCR_OK
+    basic_only = gpu.pcr_create_framebuffer(view.width, view.height)
+    with pytest.raises(gpu.PcrError):
+        gpu.pcr_resolve_both(basic_only, img_b, img_h)
+    basic_only.close()
+    fb.close()
