@@ -243,8 +243,10 @@ pcr_status pcr_framebuffer_keys(const pcr_framebuffer* fb, const uint64_t** d_ke
  *     d_images[W*H, 2*W*H), clearing fb;
  *   - copies the images to h_basic and h_hq (host, W*H u32 each; h_hq is unused without PCR_FB_HQ).
  * d_images: caller-owned device scratch of 2*W*H u32. The frame must start from a cleared fb; it leaves fb
- * cleared. Everything is enqueued on `stream`, plus fb's internal copy stream, which is ordered with
- * `stream` by events and created, with its events, by the first call on fb. The call returns at once:
+ * cleared. Everything is enqueued on `stream`, plus the device's upload queue: one internal copy stream per
+ * device, shared by all framebuffers, so that frames from host memory upload back to back in call order and
+ * each frame's passes overlap the next frame's upload. It is ordered with `stream` by events (created by the
+ * first call on fb); a frame's copies also wait for the work queued on `stream` before the call. Returns at once:
  * synchronise `stream` before reading the host images or reusing h_points or d_points. Requirements as for
  * pcr_render_hq_splat (HQ) or pcr_render_atomicmin. */
 pcr_status pcr_render_frame_host(pcr_framebuffer* fb, const pcr_point* h_points, uint64_t n, const pcr_view* view,

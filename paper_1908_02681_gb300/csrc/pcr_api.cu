@@ -31,8 +31,8 @@ struct pcr_framebuffer {
   long long* d_table;
   pcr::DevView table_view;
   bool table_valid;
-  // frames from host memory (pcr_render_frame_host): copy stream and events, created by its first call
-  cudaStream_t copy_stream;
+  // frames from host memory (pcr_render_frame_host): events, created by its first call (the copies go to the
+  // device's upload queue, upload_stream)
   cudaEvent_t copy_events[9];  // [0]: start of the frame on the caller's stream; [1..8]: chunk k landed
   // band mask (pass 1 -> pass 2, see pcr::BandMask): two words per 64 points, grown on demand; valid for the
   // points, count, view and eps of the pass 1 that wrote it, until the framebuffer is cleared
@@ -351,10 +351,8 @@ pcr_status pcr_destroy_framebuffer(pcr_framebuffer* fb) {
   cudaFree(fb->status);
   cudaFree(fb->d_table);
   cudaFree(fb->band_mask);
-  if (fb->copy_stream) {
-    cudaStreamDestroy(fb->copy_stream);
-    for (cudaEvent_t e : fb->copy_events) cudaEventDestroy(e);
-  }
+  for (cudaEvent_t e : fb->copy_events)
+    if (e) cudaEventDestroy(e);
   cudaSetDevice(prev);
   delete fb;
   return PCR_OK;
@@ -642,6 +640,28 @@ pcr_status pcr_get_device_status(pcr_framebuffer* fb, pcr_stream_t stream) {
   return PCR_OK;
 }
 
+namespace {
+
+// The device's upload queue for frames from host memory: their copies share the host-to-device link, so they
+// run back to back in call order, and each frame's passes overlap the next frame's upload. (With one copy
+// stream per framebuffer, two frames in flight uploaded side by side, finished together, and left the link idle
+// while both computed: 91-92 % of the link's rate end to end.) Created by the first frame on the device; lives
+// as long as the process.
+cudaStream_t upload_stream(int device, cudaError_t* err) {
+  static std::mutex mu;
+  static cudaStream_t streams[64] = {};
+  std::lock_guard<std::mutex> lock(mu);
+  *err = cudaSuccess;
+  if (device < 0 || device >= 64) {
+    *err = cudaErrorInvalidDevice;
+    return nullptr;
+  }
+  if (!streams[device]) *err = cudaStreamCreateWithFlags(&streams[device], cudaStreamNonBlocking);
+  return streams[device];
+}
+
+}  // namespace
+
 pcr_status pcr_render_frame_host(pcr_framebuffer* fb, const pcr_point* h_points, uint64_t n, const pcr_view* view,
                                  uint32_t eps_num, uint32_t eps_den, uint32_t background_rgba, pcr_point* d_points,
                                  uint32_t* d_images, uint32_t* h_basic, uint32_t* h_hq, pcr_stream_t stream) {
@@ -658,22 +678,21 @@ pcr_status pcr_render_frame_host(pcr_framebuffer* fb, const pcr_point* h_points,
   if (!d_images || !h_basic || (hq && !h_hq)) return fail(PCR_ERR_INVALID_ARG, "d_images and the host images are required");
   const cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaSuccess;
-  if (!fb->copy_stream) {  // first call on this framebuffer
-    e = cudaStreamCreateWithFlags(&fb->copy_stream, cudaStreamNonBlocking);
+  const cudaStream_t up = upload_stream(fb->device, &e);
+  if (e != cudaSuccess) return cuda_fail(e, "upload stream");
+  if (!fb->copy_events[8]) {  // first call on this framebuffer
     for (int k = 0; k < 9 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&fb->copy_events[k], cudaEventDisableTiming);
     if (e != cudaSuccess) {
-      if (fb->copy_stream) cudaStreamDestroy(fb->copy_stream);
       for (cudaEvent_t& ev : fb->copy_events) {
         if (ev) cudaEventDestroy(ev);
         ev = nullptr;
       }
-      fb->copy_stream = nullptr;
-      return cuda_fail(e, "copy stream");
+      return cuda_fail(e, "copy events");
     }
   }
   // the copies into d_points wait for earlier work on the caller's stream (which may still read them)
   e = cudaEventRecord(fb->copy_events[0], s);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(fb->copy_stream, fb->copy_events[0], 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(up, fb->copy_events[0], 0);
   if (e != cudaSuccess) return cuda_fail(e, "frame start");
   // up to 8 chunks: pass 1 of chunk k runs while chunk k + 1 is still being copied. Chunk bounds are multiples
   // of 64 points, so that each chunk's band mask (HQ frames) is its part of the frame's mask.
@@ -686,9 +705,8 @@ pcr_status pcr_render_frame_host(pcr_framebuffer* fb, const pcr_point* h_points,
   for (uint64_t k = 0; k < chunks && n > 0; ++k) {
     const uint64_t lo = bound(k), hi = bound(k + 1);
     if (hi == lo) continue;
-    e = cudaMemcpyAsync(d_points + lo, h_points + lo, (hi - lo) * sizeof(pcr_point), cudaMemcpyHostToDevice,
-                        fb->copy_stream);
-    if (e == cudaSuccess) e = cudaEventRecord(fb->copy_events[1 + k], fb->copy_stream);
+    e = cudaMemcpyAsync(d_points + lo, h_points + lo, (hi - lo) * sizeof(pcr_point), cudaMemcpyHostToDevice, up);
+    if (e == cudaSuccess) e = cudaEventRecord(fb->copy_events[1 + k], up);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, fb->copy_events[1 + k], 0);
     if (e != cudaSuccess) return cuda_fail(e, "point upload");
     band.tile_offset = lo / pcr::kTile;
