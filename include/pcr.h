@@ -124,8 +124,8 @@ typedef struct {
                                24 B per pixel) and tests each decided code q by lo <= q <= hi, where the host
                                finds eps_num * (2^40 + Nq) + eps_den * 2^40 <= 2^64 (the same decision as the
                                band test of pcr_render_hq_splat then); 0 (default): the band test on the stored
-                               key. Faster for points in random order without band records (pass 2 about 6 %),
-                               slower by the extra kernel in scan order; the autotuner tries both. */
+                               key. Faster for points in random order without band records (pass 2 about 1 %),
+                               slower in scan order (about 3 %); the autotuner tries both. */
 } pcr_tuning;
 
 /* Framebuffer flags. */
