@@ -121,20 +121,22 @@ typedef struct {
   uint32_t band_eps_num, band_eps_den; /* eps of the records (default 1 / 100); band_eps_den in 1..2^20 */
   int32_t band_bounds;      /* 1: pass 2 with the exact transform first turns each pixel's qmin into its accept
                                bounds {qmin, qmin + floor(eps_num * (qmin + Nq) / eps_den)} (one more kernel,
-                               24 B per pixel) and tests each decided code q by lo <= q <= hi, where the host
-                               finds eps_num * (2^40 + Nq) + eps_den * 2^40 <= 2^64 (the same decision as the
-                               band test of pcr_render_hq_splat then); 0 (default): the band test on the stored
-                               key. Faster for points in random order without band records (pass 2 about 1 %),
-                               slower in scan order (about 3 %); the autotuner tries both. */
+                               24 B per pixel of traffic) and tests each decided code q by lo <= q <= hi, where
+                               the host finds eps_num * (2^40 + Nq) + eps_den * 2^40 <= 2^64 (the same decision
+                               as the band test of pcr_render_hq_splat then). The first such pass allocates
+                               16 B per pixel (not during stream capture: there the stored-key test is used).
+                               0 (default): the band test on the stored key. Faster for points in random order
+                               without band records (pass 2 about 1 %), slower in scan order (about 3 %); the
+                               autotuner tries both. */
 } pcr_tuning;
 
 /* Framebuffer flags. */
-#define PCR_FB_HQ 1u /* also allocate the HQ buffers, 32 B/pixel (needed by pcr_render_hq_splat) */
+#define PCR_FB_HQ 1u /* also allocate the 16 B/pixel HQ accumulation buffer (needed by pcr_render_hq_splat) */
 
 /* Allocates a width x height framebuffer on the current device (keys: 8 B/pixel; with PCR_FB_HQ also
- * sums: 16 B/pixel, and pass 2's per-pixel band bounds: 16 B/pixel; plus a 96 KB device copy of the depth tables of the view last rendered, re-uploaded on
- * the render call's stream when the view changes) and clears it (synchronously). width, height in
- * 1..16384. */
+ * sums: 16 B/pixel, and 16 B/pixel of band bounds once a pass 2 runs with pcr_tuning.band_bounds; plus a
+ * 96 KB device copy of the depth tables of the view last rendered, re-uploaded on the render call's stream
+ * when the view changes) and clears it (synchronously). width, height in 1..16384. */
 pcr_status pcr_create_framebuffer(int32_t width, int32_t height, uint32_t flags, pcr_framebuffer** out);
 
 /* Frees the framebuffer (synchronises the device first). NULL is accepted. */

@@ -23,7 +23,8 @@ struct pcr_framebuffer {
   int device;
   unsigned long long* keys;  // width * height
   ulonglong2* accum;         // width * height (HQ only)
-  ulonglong2* bounds;        // width * height (HQ only): pass 2's per-pixel accept bounds (pcr::k_band_bounds)
+  ulonglong2* bounds;        // width * height (HQ only, allocated by the first pass 2 with band_bounds): pass 2's
+                             // per-pixel accept bounds (pcr::k_band_bounds)
   uint32_t* status;          // device status word
   pcr::Tuning tuning;        // launch tuning of the point passes
   // device copy of the depth table of the view last rendered with the certified transform (loaded by the
@@ -266,6 +267,22 @@ pcr_status launch_raster_band(pcr_framebuffer* fb, const pcr_point* d_points, ui
   return PCR_OK;
 }
 
+// The framebuffer's per-pixel band bounds, allocated by the first call (outside stream capture only); null when
+// they cannot be (pass 2 then tests against the stored keys).
+ulonglong2* bounds_buffer(pcr_framebuffer* fb, cudaStream_t s) {
+  if (fb->bounds) return fb->bounds;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (cudaMalloc(&fb->bounds, (uint64_t)fb->width * fb->height * sizeof(ulonglong2)) != cudaSuccess) {
+    cudaGetLastError();
+    fb->bounds = nullptr;
+  }
+  return fb->bounds;
+}
+
 pcr_status launch_hq(pcr_framebuffer* fb, const pcr_point* d_points, uint64_t n, const pcr::DevView& dv,
                      int transform, uint32_t eps_num, uint32_t eps_den, cudaStream_t s) {
   const uint4* pts = reinterpret_cast<const uint4*>(d_points);
@@ -282,7 +299,7 @@ pcr_status launch_hq(pcr_framebuffer* fb, const pcr_point* d_points, uint64_t n,
   const int launched = pcr::launch_hq_certified(pts, n, dv, transform == PCR_TRANSFORM_DOUBLE_FLOAT, fb->keys, acc,
                                                 eps_num, eps_den, fb->status, sm_count(fb->device), s, fb->tuning,
                                                 table, band ? fb->band_mask : nullptr,
-                                                fb->tuning.band_bounds ? fb->bounds : nullptr);
+                                                fb->tuning.band_bounds ? bounds_buffer(fb, s) : nullptr);
   return after_launch("k_hq_certified", (uint64_t)launched);
 }
 
@@ -309,7 +326,6 @@ pcr_status pcr_create_framebuffer(int32_t width, int32_t height, uint32_t flags,
   const uint64_t npx = (uint64_t)width * (uint64_t)height;
   e = cudaMalloc(&fb->keys, npx * sizeof(unsigned long long));
   if (e == cudaSuccess && (flags & PCR_FB_HQ)) e = cudaMalloc(&fb->accum, npx * sizeof(ulonglong2));
-  if (e == cudaSuccess && (flags & PCR_FB_HQ)) e = cudaMalloc(&fb->bounds, npx * sizeof(ulonglong2));
   if (e == cudaSuccess) e = cudaMalloc(&fb->status, 256);
   if (e == cudaSuccess) e = cudaMalloc(&fb->d_table, pcr::kMaxRanges * sizeof(pcr::CertParams::F));
   if (e != cudaSuccess) {
