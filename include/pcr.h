@@ -398,11 +398,11 @@ pcr_status pcr_batch_destroy(pcr_batch* batch);
  * PCR_ERR_INVALID_ARG, with the limit in pcr_last_error_message(), and enqueues nothing.
  *
  * The array takes about 3.4 MB on every device that loads libpcr, until the process exits. The first call
- * on each device looks up the array's address (cudaGetSymbolAddress) with that device current: make that
- * first call before any stream capture. All calls on a device share the one array, which keeps what the
- * last call left in it (each call clears what must start at zero). Calls whose work overlaps on the GPU
- * (on different streams, or from different host threads without ordering) race on the array and produce
- * wrong images: put them on one stream or synchronise between them. On the host, calls take a lock. */
+ * on each device looks up the array's address (cudaGetSymbolAddress) with that device current. All calls
+ * on a device share the one array, which keeps what the last call left in it (each call clears what must
+ * start at zero). Calls whose work overlaps on the GPU (on different streams, or from different host
+ * threads without ordering) race on the array and produce wrong images: put them on one stream or
+ * synchronise between them. On the host, calls take a lock. */
 pcr_status pcr_render_views_noalloc(const pcr_point* d_points, uint64_t n, pcr_framebuffer* const* fbs,
                                     uint32_t* const* d_outs, const pcr_view* views, int32_t count, int32_t hq,
                                     uint32_t eps_num, uint32_t eps_den, uint32_t background_rgba,
