@@ -610,8 +610,11 @@ __device__ __forceinline__ unsigned long long code_from_fixed(uint32_t a1, uint3
 // kPw (PIECEWISE depth, CertParams only): the range whose window certainly holds w gives the table (block r of
 // F), the fixed-point offset (with the range's first code folded in: base 2^40 only changes bits 40 and up,
 // not the fraction) and the margin. Outside every window: undecided.
-// kPw = 1: at most two ranges, whose constants are picked by selects (no indexed constant loads); 2: any number.
-template <typename PP, int kPw = 0>
+// kPw = 1: at most two ranges: a branch on the range (kRange, 0 or 1, selected from w) whose two arms read their
+// range's constants at fixed offsets. A warp whose points all lie in one range takes one arm; picking the
+// constants per point with selects instead cost 27 more instructions per 32 points and 8 % of pass 1 with the
+// paper's nm / um / mm ranges. kPw = 2: any number of ranges, indexed per point.
+template <typename PP, int kPw = 0, int kRange = -1>
 __device__ __forceinline__ FastFrag classify_fast(const PP& P, const long long* __restrict__ F, uint4 p) {
   const float x = __uint_as_float(p.x), y = __uint_as_float(p.y), z = __uint_as_float(p.z);
   // finite, and inside the exponent range whose table entries exist (else tier 2 decides): the rounded sum of
@@ -626,9 +629,12 @@ __device__ __forceinline__ FastFrag classify_fast(const PP& P, const long long* 
   float kd, hd0;
   int kk = 0;  // PIECEWISE: the range
   (void)kk;
+  if constexpr (kPw == 1 && kRange < 0) {
+    // one or two ranges (a single range has pw_start[1] = +inf)
+    return w >= P.pw_start[1] ? classify_fast<PP, 1, 1>(P, F, p) : classify_fast<PP, 1, 0>(P, F, p);
+  }
   if constexpr (kPw == 1) {
-    // one or two ranges (a single range has pw_start[1] = +inf): selects between the two sets of constants
-    const bool second = w >= P.pw_start[1];
+    constexpr bool second = kRange == 1;
     kk = second ? 1 : 0;
     depth_in = fabsf(__fsub_rn(w, second ? P.pw_wc[1] : P.pw_wc[0])) <
                __fmaf_rn(-P.kw, s, second ? P.pw_whk[1] : P.pw_whk[0]);

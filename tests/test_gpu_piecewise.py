@@ -1,8 +1,10 @@
 """PIECEWISE depth (Section 2.1: sub-ranges of the depth with their own resolution, e.g. nm up to 10 m, um up to
 10 km, mm beyond) through the certified single-precision transform. Every range that meets [near, far) gets
 its own fixed-point table; tier 1 decides the range from w, and what it cannot decide goes to the FP64
-definition. Framebuffers and per-point fragments must equal the oracle bit for bit, including points next to a
-range boundary and in a gap between ranges (culled by the definition)."""
+definition. Framebuffers
+and per-point fragments must equal the oracle bit for bit, including points next to a range boundary, in a gap
+between ranges (culled by the definition), and codes fine enough that many stay undecided between two
+neighbours."""
 from __future__ import annotations
 
 import numpy as np
@@ -71,6 +73,33 @@ def test_range_boundaries_point_by_point(gpu, ranges):
     assert np.array_equal(got, oracle.render_atomicmin(pts, view))
 
 
+@pytest.mark.parametrize("ranges", [
+    [[0.0, 3000.0, 3.6e8]],                              # one range, codes up to 1.08e12 (near the 2^40 cap)
+    [[0.0, 1500.0, 3.6e8], [1500.0, 3000.0, 3.6e8]],     # two ranges, the second's codes after the first's
+])
+def test_tier_two_with_coarse_codes(gpu, ranges):
+    """Codes of about 2^40 over the depth range: the FP64 definition's rounding bound of t is about 6e-4, so
+    about 0.1 % of the codes lie within it of an integer and tier 1 leaves them between two candidates (the
+    FP64 definition decides them). Per point and in the framebuffer: equal to the oracle."""
+    import torch
+    pts = scenes.lidar(2_000_003, 74)
+    view = _view(scenes.lidar_1km_view(), ranges, 640, 360)
+    dev = _dev(pts)
+    pix, key = gpu.pcr_project_points(dev, view)
+    o_pix, _, o_key = oracle.project(pts, view)
+    pix = pix.cpu().numpy().astype(np.int64)
+    key = key.cpu().numpy().view(np.uint64)
+    bad = np.flatnonzero((pix != o_pix) | (key != o_key))
+    assert bad.size == 0, (bad.size, bad[:5])
+    counts = torch.zeros(4, dtype=torch.int64, device="cuda")
+    got = _render(gpu, dev, view, counts)
+    assert np.array_equal(got, oracle.render_atomicmin(pts, view))
+    tier1, amb, fp64, deferred = (int(c) for c in counts.cpu())
+    print(f"\ncoarse piecewise codes: tier-1 exact {tier1}, undecided code {amb}, deferred {deferred}, "
+          f"FP64 definition {fp64} of {len(pts)}")
+    assert amb > 500 and deferred >= amb and fp64 <= deferred
+
+
 def test_eight_ranges_and_the_cap(gpu):
     pts = scenes.lidar(1_000_003, 73)
     dev = _dev(pts)
@@ -86,7 +115,7 @@ def test_eight_ranges_and_the_cap(gpu):
 
 def test_pass1_time_against_linear(gpu):
     """Pass 1 on the 100M-point LIDAR frame (1920x1080) with the paper's nm/um/mm ranges against the same frame
-    with LINEAR depth (printed; the piecewise pass must stay within 22 % of the linear one: measured 17 %)."""
+    with LINEAR depth (printed; the piecewise pass must stay within 15 % of the linear one: measured 7 %)."""
     import torch
     n = 100_000_000
     host = torch.empty((n, 4), dtype=torch.int32, pin_memory=True)
@@ -111,4 +140,4 @@ def test_pass1_time_against_linear(gpu):
         fb.close()
     print(f"\npass 1, 100M LIDAR points: linear {times['linear']:.3f} ms, piecewise {times['piecewise']:.3f} ms "
           f"({times['piecewise'] / times['linear']:.3f}x)")
-    assert times["piecewise"] < 1.22 * times["linear"], times
+    assert times["piecewise"] < 1.15 * times["linear"], times
