@@ -385,7 +385,8 @@ inline bool prepare_cert(const DevView& v, bool approximate, CertParams* P,
       ++n;
     }
     if (n == 0) return false;  // nothing of [near, far) has a code: every point is culled (FP64 kernels)
-    if (n == 1) P->pw_start[1] = 3.4e38f * 2.0f;  // +inf: the second of two selectable ranges never applies
+    // one range: NaN, so that no w (+inf included) selects the second arm, whose table the kernels do not hold
+    if (n == 1) P->pw_start[1] = std::nanf("");
     P->n_pw = n;
     P->xyz_max = xyz_limit(emin);
     std::memcpy(P->F, tables[0], sizeof(P->F));
@@ -630,7 +631,7 @@ __device__ __forceinline__ FastFrag classify_fast(const PP& P, const long long* 
   int kk = 0;  // PIECEWISE: the range
   (void)kk;
   if constexpr (kPw == 1 && kRange < 0) {
-    // one or two ranges (a single range has pw_start[1] = +inf)
+    // one or two ranges (a single range has pw_start[1] = NaN: the second arm is never selected)
     return w >= P.pw_start[1] ? classify_fast<PP, 1, 1>(P, F, p) : classify_fast<PP, 1, 0>(P, F, p);
   }
   if constexpr (kPw == 1) {

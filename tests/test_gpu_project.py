@@ -88,15 +88,22 @@ def test_city_sample(gpu):
 
 
 def test_piecewise_depth_and_special_values(gpu):
-    """Piecewise depth (the FP64 path for every transform), and NaN / infinity / huge coordinates."""
-    v = axis_view(depth_mode=2)
-    v.ranges = np.array([[0.5, 1.0, 1e9], [1.0, 8.5, 1e6]])
+    """Piecewise depth with one, two and three ranges (the exact transform selects each range's constants by a
+    branch on w), and NaN / infinity / huge coordinates: z = -inf gives w = +inf on this camera, which must not
+    select a range the view does not have."""
     rng = np.random.default_rng(9)
     xyz = np.column_stack([rng.uniform(-6, 6, 20000), rng.uniform(-6, 6, 20000), rng.uniform(-9, 0, 20000)])
     pts = pack(xyz, np.full(20000, rgba(1, 2, 3)))
-    _check(gpu, pts, v, transforms=(0, 1, 2))
     special = pack([[np.nan, 0, -1], [np.inf, 0, -1], [0, -np.inf, -1], [1e38, 1e38, -1e38], [0, 0, -0.5],
-                    [0, 0, -8.5], [-1, -1, -1], [0.999, 0.999, -1]], np.full(8, rgba(9, 8, 7)))
+                    [0, 0, -8.5], [-1, -1, -1], [0.999, 0.999, -1], [0, 0, -np.inf], [0, 0, -3.4e38],
+                    [0.5, 0.5, -3.4e38]], np.full(11, rgba(9, 8, 7)))
+    for ranges in ([[0.5, 8.5, 1e6]],
+                   [[0.5, 1.0, 1e9], [1.0, 8.5, 1e6]],
+                   [[0.5, 1.0, 1e9], [1.0, 4.0, 1e6], [4.0, 8.5, 1e5]]):
+        v = axis_view(depth_mode=2)
+        v.ranges = np.array(ranges)
+        _check(gpu, pts, v, transforms=(0, 1, 2))
+        _check(gpu, special, v)
     _check(gpu, special, axis_view())
 
 
